@@ -1,0 +1,242 @@
+/*
+ * libsvt — GB300 (sm_103a) implementation of the data-parallel hot path of the Singular Value
+ * Thresholding algorithm for matrix completion (Cai, Candes & Shen, "A Singular Value
+ * Thresholding Algorithm for Matrix Completion", 2008).
+ *
+ * One SVT iteration (Sec. 2.2, eq. (2.7); Algorithm 1 of Sec. 5.1.5):
+ *     X^k = D_tau(Y^{k-1})                      shrink: soft-threshold the singular values
+ *     Y^k = Y^{k-1} + delta P_Omega(M - X^k)    dual step on the sampled set Omega only
+ * D_tau(Y) = U diag((sigma_i - tau)_+) V^T (Sec. 2.1, eq. (2.2)) is evaluated by a
+ * rank-adaptive block Lanczos partial SVD of the sparse iterate (Sec. 5.1.1), X^k is kept as
+ * factors and evaluated on Omega only, and the dual step, the residual of eq. (5.5) and the
+ * stop test are fused into one pass over Omega.
+ *
+ * Conventions for every entry point
+ *   - Dimensions: m = number of rows (n1 in the paper), n = number of columns (n2); the paper
+ *     writes m for |Omega|, called nnz here.
+ *   - Matrices are row-major.  Index arrays are int32 and zero-based.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global memory of the
+ *     current device.  The library copies every input it keeps; the caller keeps ownership of
+ *     every buffer it passes.  Outputs are written to caller-allocated buffers.
+ *   - Every call returns an svt_status.  No call aborts, exits or traps the GPU.  After an
+ *     error, svt_last_error(ctx) returns a message (or svt_last_error(NULL) for calls that
+ *     failed before a context existed).
+ *   - Work is issued on the stream given in svt_options.stream (0 = legacy default stream);
+ *     calls that return host data synchronise that stream.
+ *   - A context is single-threaded.  Distinct contexts may be used concurrently from distinct
+ *     threads on distinct streams.
+ */
+#ifndef SVT_H_
+#define SVT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct svt_ctx svt_ctx;
+
+typedef enum svt_status {
+  SVT_OK = 0,
+  SVT_ERR_ARG = 1,            /* invalid argument (size, pointer, option, index out of range) */
+  SVT_ERR_DUP_INDEX = 2,      /* the same (row, col) pair appears twice in Omega */
+  SVT_ERR_OOM = 3,            /* device or host allocation failed */
+  SVT_ERR_CUDA = 4,           /* a CUDA runtime call failed (message has the CUDA error) */
+  SVT_ERR_RANK_LIMIT = 5,     /* more than max_rank singular values exceed tau */
+  SVT_ERR_NOT_CONVERGED = 6,  /* k_max iterations without meeting the stopping rule */
+  SVT_ERR_NUMERIC = 7,        /* NaN/Inf or loss of positive definiteness in the Lanczos basis */
+  SVT_ERR_TIMEOUT = 8,        /* a bounded device wait expired */
+  SVT_ERR_INTERNAL = 9,       /* internal consistency check failed */
+  SVT_STOPPED = 10            /* svt_step: the stopping rule eq. (5.5) holds at this iterate */
+} svt_status;
+
+/* Arithmetic of the per-nonzero work (Y, M values, the two sparse products, X on Omega and the
+ * dual step).  The Lanczos basis, its reorthogonalisation and the projected SVD that fixes the
+ * singular values compared against tau are float64 in every mode. */
+enum { SVT_FP64 = 0, SVT_FP32 = 1 };
+
+typedef struct svt_options {
+  int precision;          /* SVT_FP64 (default) or SVT_FP32 */
+  int block;              /* Lanczos block size b (multiple of 8, <= 32); 0 = automatic */
+  int ell;                /* rank increment l of Sec. 5.1.1 (default 5) */
+  int k_max;              /* maximum SVT iterations after the kick (default 1000) */
+  int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J*b <= 96) */
+  int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
+  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-10 FP64, 1e-6 FP32) */
+  int indices_on_device;  /* rows/cols/M_omega given to svt_create are device pointers */
+  uint64_t seed;          /* seed of the random start columns of the Lanczos blocks */
+  void* stream;           /* cudaStream_t to issue work on; NULL = default stream */
+} svt_options;
+
+/* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
+typedef struct svt_step_info {
+  int64_t k;              /* iteration index after the kick (1-based) */
+  int r;                  /* r_k = #{sigma_j(Y^{k-1}) > tau} */
+  int s;                  /* s_k: triplets computed in the final pass of the rank policy */
+  int passes;             /* passes of the repeat-until loop of the rank policy */
+  int lanczos_cycles;     /* restarted Lanczos cycles used by this shrink */
+  int spmm_calls;         /* sparse products (Y V and Y^T U) issued by this shrink */
+  double residual;        /* ||P_Omega(X^k - M)||_F / ||P_Omega M||_F  (eq. (5.5)) */
+  double sigma1;          /* largest singular value of Y^{k-1} */
+  double ms;              /* wall time of the step on the device (CUDA events), milliseconds */
+} svt_step_info;
+
+/* Per-solve record. */
+typedef struct svt_result {
+  int64_t iterations;     /* k at exit of Algorithm 1 (after the kick) */
+  int64_t k0;             /* kick count of eq. (5.3) */
+  int rank;               /* rank of X^opt */
+  int converged;          /* 1 if the stopping rule eq. (5.5) was met */
+  double residual;        /* final ||P_Omega(X - M)||_F / ||P_Omega M||_F */
+  double norm2_M;         /* ||P_Omega M||_2 (Sec. 5.1.3) */
+  double normF_M;         /* ||P_Omega M||_F */
+  double ms;              /* wall time of the solve (kick + iterations), milliseconds */
+  int64_t spmm_calls;     /* total sparse products */
+  int64_t lanczos_cycles; /* total Lanczos cycles */
+} svt_result;
+
+/* Fills *opt with the defaults listed above. */
+void svt_default_options(svt_options* opt);
+
+/*
+ * Builds a context for one completion problem: stores Omega (Sec. 2.2: Y^k vanishes off Omega,
+ * so only Omega is ever stored) in row-major (CSR) and column-major (CSC) order with the
+ * permutation between them, and the sampled entries M_ij, (i,j) in Omega.
+ *   m, n       matrix dimensions (n1, n2), 1 <= m, n < 2^31, m*n < 2^62
+ *   nnz        |Omega|, 1 <= nnz < 2^31
+ *   rows, cols nnz indices each, any order; host pointers, or device pointers when
+ *              opt->indices_on_device
+ *   M_omega    nnz sampled values (float64), same order as rows/cols, same memory space
+ *   opt        may be NULL (defaults)
+ *   out        receives the context; NULL on error
+ * Errors: SVT_ERR_ARG (bad sizes, NULL pointers, an index outside [0,m) x [0,n)),
+ * SVT_ERR_DUP_INDEX (a pair given twice), SVT_ERR_OOM, SVT_ERR_CUDA.
+ */
+svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                      const double* M_omega, const svt_options* opt, svt_ctx** out);
+
+/* Releases all device and host memory of the context.  NULL is ignored. */
+void svt_destroy(svt_ctx* ctx);
+
+/* Message of the last error on ctx (or of the last failed svt_create when ctx is NULL). */
+const char* svt_last_error(const svt_ctx* ctx);
+
+/*
+ * Sets the parameters of Algorithm 1 (Sec. 5.1.5) and applies the kicking device of Sec. 5.1.3:
+ * computes ||P_Omega M||_2 by the Lanczos partial SVD, k0 = the integer with
+ * tau / (delta ||P_Omega M||_2) in (k0 - 1, k0] (eq. (5.3)), and sets Y^0 = k0 delta P_Omega M,
+ * r_0 = 0, k = 0.
+ *   tau       threshold; <= 0 selects 5 sqrt(m n) (Sec. 5.2.1: tau = 5n for square matrices)
+ *   delta     step size; <= 0 selects 1.2 m n / nnz (eq. (5.1))
+ *   eps       tolerance of the stopping rule eq. (5.5); <= 0 selects 1e-4
+ *   max_rank  capacity for the rank of X^k (1 .. 64); exceeding it returns SVT_ERR_RANK_LIMIT
+ *   k0        >= 0 uses this kick count instead of eq. (5.3); -1 = eq. (5.3)
+ * Errors: SVT_ERR_ARG, SVT_ERR_NUMERIC, SVT_ERR_CUDA.
+ */
+svt_status svt_configure(svt_ctx* ctx, double tau, double delta, double eps, int max_rank, int64_t k0);
+
+/*
+ * One pass of the for-loop body of Algorithm 1: rank policy s_k = r_{k-1} + 1, then + l until a
+ * computed singular value is <= tau (Sec. 5.1.1); X^k = sum_{j<=r_k} (sigma_j - tau) u_j v_j^T;
+ * residual eq. (5.5); if residual <= eps returns SVT_STOPPED and leaves Y unchanged (the
+ * break of Algorithm 1), else commits Y^k = Y^{k-1} + delta P_Omega(M - X^k) and returns SVT_OK.
+ * info may be NULL.  Requires a prior svt_configure (or svt_solve).
+ */
+svt_status svt_step(svt_ctx* ctx, svt_step_info* info);
+
+/*
+ * Algorithm 1 in full: svt_configure(ctx, tau, delta, eps, max_rank, -1) followed by svt_step
+ * until SVT_STOPPED or k_max iterations.  Returns SVT_OK when the stopping rule was met,
+ * SVT_ERR_NOT_CONVERGED after k_max iterations (factors of the last iterate are kept), or the
+ * first error of a step.  out may be NULL.
+ */
+svt_status svt_solve(svt_ctx* ctx, double tau, double delta, double eps, int max_rank, svt_result* out);
+
+/* Rank r of the current X^k (0 before the first step). */
+svt_status svt_get_rank(const svt_ctx* ctx, int* r);
+
+/*
+ * Copies X^k = U diag(d) V^T in factored form (X^opt of Algorithm 1 after svt_solve):
+ *   U  host, m x capacity_r row-major (first r columns written), or NULL
+ *   d  host, capacity_r values sigma_j - tau > 0 (first r written), or NULL
+ *   V  host, n x capacity_r row-major (first r columns written), or NULL
+ * Columns are the singular vectors of Y^{k-1} for its r largest singular values, in decreasing
+ * order.  Errors: SVT_ERR_ARG if capacity_r < r.
+ */
+svt_status svt_get_factors(svt_ctx* ctx, double* U, double* d, double* V, int capacity_r);
+
+/* Copies the current dual iterate Y on Omega, in row-major (sorted (row, col)) order, to the
+ * host array y (nnz values). */
+svt_status svt_get_Y(svt_ctx* ctx, double* y);
+
+/* Replaces the current dual iterate by the host array y (nnz values in sorted row-major order).
+ * Used to apply one shrink (svt_shrink) to a given sparse matrix supported on Omega. */
+svt_status svt_set_Y(svt_ctx* ctx, const double* y);
+
+/*
+ * Copies the stored structure of Omega to host arrays (each may be NULL):
+ *   row_ptr[m+1], col_idx[nnz]        row-major order, columns increasing within a row
+ *   col_ptr[n+1], row_idx[nnz]        column-major order, rows increasing within a column
+ *   csc_to_csr[nnz]                   row-major position of each column-major entry
+ */
+svt_status svt_get_structure(svt_ctx* ctx, int32_t* row_ptr, int32_t* col_idx, int32_t* col_ptr,
+                             int32_t* row_idx, int32_t* csc_to_csr);
+
+/*
+ * X = D_tau(Y) of the current dual iterate (Sec. 2.1, eq. (2.2)) by the Lanczos partial SVD,
+ * without a dual step: computes the factors of D_tau(Y), stores them as the current X, and
+ * returns their rank in *r (may be NULL).  The singular values of Y larger than tau are written
+ * to the host array sigma (capacity max_rank, may be NULL).  tau <= 0 uses the configured tau.
+ */
+svt_status svt_shrink(svt_ctx* ctx, double tau, int* r, double* sigma);
+
+/*
+ * Kernel-level entry points on the context's Omega (device pointers, row-major dense blocks
+ * with b columns, 1 <= b <= 64):
+ *   svt_apply_Y   W (m x b, float64) = Y V  for V (n x b, float64)   -- Y times a block
+ *   svt_apply_Yt  Z (n x b, float64) = Y^T U for U (m x b, float64)  -- Y transpose times a block
+ * Y is the current dual iterate; the arithmetic is that of the context's precision.  These are
+ * the two products the Lanczos bidiagonalisation needs (Sec. 2.2 and Sec. 5.1.1).
+ */
+svt_status svt_apply_Y(svt_ctx* ctx, const double* V, int b, double* W);
+svt_status svt_apply_Yt(svt_ctx* ctx, const double* U, int b, double* Z);
+
+/*
+ * Fused evaluation of X on Omega and the dual step (Algorithm 1, the residual test and the
+ * update of Y; eq. (5.5)) for given device factors Ut (m x r, row-major; Ut = U diag(d)) and
+ * V (n x r): for every (i,j) in Omega, x = sum_t Ut[i,t] V[j,t], e = M_ij - x,
+ * y_out[p] = y_in[p] + delta e (row-major order p), and *res2 (host) = sum e^2.
+ * y_in, y_out: device, nnz float64 each, row-major order (may alias).
+ */
+svt_status svt_sddmm_update(svt_ctx* ctx, const double* Ut, const double* V, int r, double delta,
+                            const double* y_in, double* y_out, double* res2);
+
+/*
+ * Random-keys sampler of Omega on the device (Sec. 5.2.1: Omega uniform among all subsets of
+ * cardinality nnz): the nnz linear ids i*n + j in [0, m n) with the smallest (key, id), where
+ * key(id) is output number id + 1 of SplitMix64 (Steele, Lea & Flood 2014) started at state
+ * `seed`.  Writes rows/cols (device, nnz int32 each) sorted by id, i.e. row-major.
+ * Allocates its own scratch (O(nnz) device memory) and frees it before returning; synchronises
+ * `stream` (cudaStream_t, NULL = default).  Errors: SVT_ERR_ARG, SVT_ERR_OOM, SVT_ERR_CUDA.
+ */
+svt_status svt_sample_omega(int64_t m, int64_t n, int64_t nnz, uint64_t seed, int32_t* rows, int32_t* cols,
+                            void* stream);
+
+/*
+ * Snapshot of the solver state (k, r, parameters, Y on Omega, factors of X, warm-start block)
+ * into a host buffer.  With buf == NULL, *bytes receives the size needed.  svt_load_state
+ * restores a snapshot taken from a context with the same Omega and precision, so that the
+ * following iterates are bit-identical to an uninterrupted run.
+ */
+svt_status svt_save_state(svt_ctx* ctx, void* buf, size_t* bytes);
+svt_status svt_load_state(svt_ctx* ctx, const void* buf, size_t bytes);
+
+/* Device kernels launched by this library so far on ctx (for launch accounting). */
+int64_t svt_kernel_launches(const svt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVT_H_ */

@@ -1,0 +1,224 @@
+"""GB300-native Singular Value Thresholding (Cai, Candes & Shen 2008): Python binding of libsvt.
+
+Thin marshalling layer over the C-ABI in include/svt.h.  Every step of the SVT hot path runs in
+the library's CUDA kernels; PyTorch is used here only to hold device buffers and to name the
+CUDA stream.  If libsvt.so is missing, the calls raise (there is no CPU fallback).
+
+    from paper_0810_3286_gb300 import Solver
+    s = Solver(m, n, rows, cols, m_vals, precision="fp64")   # numpy or torch inputs
+    res = s.solve(tau, delta, eps=1e-4, max_rank=20)
+    U, d, V = s.factors()                                    # X = U diag(d) V^T
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+from ._abi import (SVT_ERR_NOT_CONVERGED, SVT_FP32, SVT_FP64, SVT_OK, SVT_STOPPED, SVTError, svt_options,
+                   svt_result, svt_step_info)
+
+__all__ = ["Solver", "SVTError", "sample_omega", "library", "SVT_FP64", "SVT_FP32", "StepInfo", "SolveResult"]
+
+
+def library():
+    """The loaded libsvt (raises if it has not been built)."""
+    return _abi.load()
+
+
+def _check(status: int, where: str, ctx=None, allow=()):
+    if status == SVT_OK or status in allow:
+        return status
+    L = library()
+    msg = L.svt_last_error(ctx).decode(errors="replace")
+    raise SVTError(status, where, msg)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array (host) or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected numpy array or torch tensor")
+
+
+class StepInfo(dict):
+    pass
+
+
+class SolveResult(dict):
+    pass
+
+
+class Solver:
+    """One completion problem: Omega, the sampled entries and the SVT state (svt_ctx)."""
+
+    def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
+                 k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
+                 max_cycles: int = 40):
+        L = library()
+        opt = svt_options()
+        L.svt_default_options(ctypes.byref(opt))
+        opt.precision = {"fp64": SVT_FP64, "fp32": SVT_FP32}[precision]
+        opt.ell = ell
+        opt.k_max = k_max
+        opt.lanczos_steps = lanczos_steps
+        opt.lanczos_tol = lanczos_tol
+        opt.seed = seed
+        opt.max_cycles = max_cycles
+        sh = _stream_handle(stream)
+        opt.stream = sh
+        on_device = hasattr(rows, "is_cuda") and rows.is_cuda
+        if on_device:
+            import torch
+            if not (cols.is_cuda and m_vals.is_cuda):
+                raise ValueError("rows, cols and m_vals must be in the same memory space")
+            if rows.dtype != torch.int32 or cols.dtype != torch.int32 or m_vals.dtype != torch.float64:
+                raise TypeError("device inputs must be int32, int32, float64")
+            opt.indices_on_device = 1
+            keep = (rows, cols, m_vals)
+        else:
+            if hasattr(rows, "numpy"):
+                rows, cols, m_vals = rows.numpy(), cols.numpy(), m_vals.numpy()
+            keep = (np.ascontiguousarray(rows, dtype=np.int32), np.ascontiguousarray(cols, dtype=np.int32),
+                    np.ascontiguousarray(m_vals, dtype=np.float64))
+        self.m, self.n = int(m), int(n)
+        self.nnz = int(keep[0].shape[0])
+        self.precision = precision
+        ctx = ctypes.c_void_p()
+        st = L.svt_create(self.m, self.n, self.nnz, _ptr(keep[0]), _ptr(keep[1]), _ptr(keep[2]), ctypes.byref(opt),
+                          ctypes.byref(ctx))
+        _check(st, "svt_create", None)
+        self._ctx = ctx
+        self._L = L
+
+    # -- lifetime --------------------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._L.svt_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- Algorithm 1 -----------------------------------------------------------------------------
+    def configure(self, tau: float = 0.0, delta: float = 0.0, eps: float = 1e-4, max_rank: int = 27, k0: int = -1):
+        _check(self._L.svt_configure(self._ctx, tau, delta, eps, max_rank, k0), "svt_configure", self._ctx)
+
+    def step(self) -> StepInfo:
+        info = svt_step_info()
+        st = self._L.svt_step(self._ctx, ctypes.byref(info))
+        _check(st, "svt_step", self._ctx, allow=(SVT_STOPPED,))
+        out = StepInfo({f: getattr(info, f) for f, _ in svt_step_info._fields_})
+        out["stopped"] = st == SVT_STOPPED
+        return out
+
+    def solve(self, tau: float = 0.0, delta: float = 0.0, eps: float = 1e-4, max_rank: int = 27,
+              raise_on_nonconvergence: bool = True) -> SolveResult:
+        res = svt_result()
+        st = self._L.svt_solve(self._ctx, tau, delta, eps, max_rank, ctypes.byref(res))
+        allow = () if raise_on_nonconvergence else (SVT_ERR_NOT_CONVERGED,)
+        _check(st, "svt_solve", self._ctx, allow=allow)
+        return SolveResult({f: getattr(res, f) for f, _ in svt_result._fields_})
+
+    def shrink(self, tau: float = 0.0):
+        """D_tau of the current Y; returns (rank, singular values > tau)."""
+        r = ctypes.c_int()
+        sig = np.zeros(64)
+        _check(self._L.svt_shrink(self._ctx, tau, ctypes.byref(r), sig.ctypes.data), "svt_shrink", self._ctx)
+        return r.value, sig[:r.value].copy()
+
+    # -- state access ----------------------------------------------------------------------------
+    def rank(self) -> int:
+        r = ctypes.c_int()
+        _check(self._L.svt_get_rank(self._ctx, ctypes.byref(r)), "svt_get_rank", self._ctx)
+        return r.value
+
+    def factors(self):
+        r = self.rank()
+        U = np.zeros((self.m, max(r, 1)))
+        d = np.zeros(max(r, 1))
+        V = np.zeros((self.n, max(r, 1)))
+        _check(self._L.svt_get_factors(self._ctx, U.ctypes.data, d.ctypes.data, V.ctypes.data, max(r, 1)),
+               "svt_get_factors", self._ctx)
+        return U[:, :r].copy(), d[:r].copy(), V[:, :r].copy()
+
+    def get_Y(self) -> np.ndarray:
+        y = np.zeros(self.nnz)
+        _check(self._L.svt_get_Y(self._ctx, y.ctypes.data), "svt_get_Y", self._ctx)
+        return y
+
+    def set_Y(self, y) -> None:
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if y.shape != (self.nnz,):
+            raise ValueError("y must have nnz entries")
+        _check(self._L.svt_set_Y(self._ctx, y.ctypes.data), "svt_set_Y", self._ctx)
+
+    def structure(self):
+        rp = np.zeros(self.m + 1, np.int32)
+        ci = np.zeros(self.nnz, np.int32)
+        cp = np.zeros(self.n + 1, np.int32)
+        ri = np.zeros(self.nnz, np.int32)
+        c2r = np.zeros(self.nnz, np.int32)
+        _check(self._L.svt_get_structure(self._ctx, rp.ctypes.data, ci.ctypes.data, cp.ctypes.data, ri.ctypes.data,
+                                         c2r.ctypes.data), "svt_get_structure", self._ctx)
+        return rp, ci, cp, ri, c2r
+
+    # -- kernel-level entry points (torch device tensors, float64, contiguous) -------------------
+    def apply_Y(self, V, W):
+        _check(self._L.svt_apply_Y(self._ctx, _ptr(V), int(V.shape[1]), _ptr(W)), "svt_apply_Y", self._ctx)
+
+    def apply_Yt(self, U, Z):
+        _check(self._L.svt_apply_Yt(self._ctx, _ptr(U), int(U.shape[1]), _ptr(Z)), "svt_apply_Yt", self._ctx)
+
+    def sddmm_update(self, Ut, V, delta: float, y_in, y_out) -> float:
+        res2 = ctypes.c_double()
+        r = int(Ut.shape[1]) if Ut is not None else 0
+        _check(self._L.svt_sddmm_update(self._ctx, _ptr(Ut) if r else None, _ptr(V) if r else None, r, delta,
+                                        _ptr(y_in), _ptr(y_out), ctypes.byref(res2)), "svt_sddmm_update", self._ctx)
+        return res2.value
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        _check(self._L.svt_save_state(self._ctx, None, ctypes.byref(n)), "svt_save_state", self._ctx)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._L.svt_save_state(self._ctx, buf, ctypes.byref(n)), "svt_save_state", self._ctx)
+        return buf.raw[:n.value]
+
+    def load_state(self, blob: bytes) -> None:
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._L.svt_load_state(self._ctx, buf, len(blob)), "svt_load_state", self._ctx)
+
+    def kernel_launches(self) -> int:
+        return int(self._L.svt_kernel_launches(self._ctx))
+
+
+def sample_omega(m: int, n: int, nnz: int, seed: int, rows_out, cols_out, stream=None) -> None:
+    """Device random-keys sampler of Omega into int32 device tensors rows_out/cols_out."""
+    L = library()
+    _check(L.svt_sample_omega(m, n, nnz, seed & (2**64 - 1), _ptr(rows_out), _ptr(cols_out),
+                              _stream_handle(stream)), "svt_sample_omega", None)

@@ -1,0 +1,138 @@
+"""ctypes declarations of the libsvt C-ABI (include/svt.h).  Argument marshalling only.
+
+The shared library is loaded from paper_0810_3286_gb300/_build/libsvt.so.  There is no fallback:
+if the library is missing or cannot be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libsvt.so")
+
+SVT_OK = 0
+SVT_ERR_ARG = 1
+SVT_ERR_DUP_INDEX = 2
+SVT_ERR_OOM = 3
+SVT_ERR_CUDA = 4
+SVT_ERR_RANK_LIMIT = 5
+SVT_ERR_NOT_CONVERGED = 6
+SVT_ERR_NUMERIC = 7
+SVT_ERR_TIMEOUT = 8
+SVT_ERR_INTERNAL = 9
+SVT_STOPPED = 10
+
+STATUS_NAMES = {
+    0: "SVT_OK", 1: "SVT_ERR_ARG", 2: "SVT_ERR_DUP_INDEX", 3: "SVT_ERR_OOM", 4: "SVT_ERR_CUDA",
+    5: "SVT_ERR_RANK_LIMIT", 6: "SVT_ERR_NOT_CONVERGED", 7: "SVT_ERR_NUMERIC", 8: "SVT_ERR_TIMEOUT",
+    9: "SVT_ERR_INTERNAL", 10: "SVT_STOPPED",
+}
+
+SVT_FP64 = 0
+SVT_FP32 = 1
+
+
+class svt_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("ell", ctypes.c_int),
+        ("k_max", ctypes.c_int),
+        ("lanczos_steps", ctypes.c_int),
+        ("max_cycles", ctypes.c_int),
+        ("lanczos_tol", ctypes.c_double),
+        ("indices_on_device", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class svt_step_info(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int64),
+        ("r", ctypes.c_int),
+        ("s", ctypes.c_int),
+        ("passes", ctypes.c_int),
+        ("lanczos_cycles", ctypes.c_int),
+        ("spmm_calls", ctypes.c_int),
+        ("residual", ctypes.c_double),
+        ("sigma1", ctypes.c_double),
+        ("ms", ctypes.c_double),
+    ]
+
+
+class svt_result(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int64),
+        ("k0", ctypes.c_int64),
+        ("rank", ctypes.c_int),
+        ("converged", ctypes.c_int),
+        ("residual", ctypes.c_double),
+        ("norm2_M", ctypes.c_double),
+        ("normF_M", ctypes.c_double),
+        ("ms", ctypes.c_double),
+        ("spmm_calls", ctypes.c_int64),
+        ("lanczos_cycles", ctypes.c_int64),
+    ]
+
+
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dp = ctypes.POINTER(ctypes.c_double)
+_ctxp = ctypes.c_void_p
+
+# name -> (restype, argtypes)
+PROTOTYPES = {
+    "svt_default_options": (None, [ctypes.POINTER(svt_options)]),
+    "svt_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
+                                  ctypes.POINTER(svt_options), ctypes.POINTER(_ctxp)]),
+    "svt_destroy": (None, [_ctxp]),
+    "svt_last_error": (ctypes.c_char_p, [_ctxp]),
+    "svt_configure": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                     ctypes.c_int64]),
+    "svt_step": (ctypes.c_int, [_ctxp, ctypes.POINTER(svt_step_info)]),
+    "svt_solve": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                 ctypes.POINTER(svt_result)]),
+    "svt_get_rank": (ctypes.c_int, [_ctxp, ctypes.POINTER(ctypes.c_int)]),
+    "svt_get_factors": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, ctypes.c_int]),
+    "svt_get_Y": (ctypes.c_int, [_ctxp, _vp]),
+    "svt_set_Y": (ctypes.c_int, [_ctxp, _vp]),
+    "svt_get_structure": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, _vp, _vp]),
+    "svt_shrink": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _vp]),
+    "svt_apply_Y": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int, _vp]),
+    "svt_apply_Yt": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int, _vp]),
+    "svt_sddmm_update": (ctypes.c_int, [_ctxp, _vp, _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _dp]),
+    "svt_sample_omega": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, _vp, _vp,
+                                        _vp]),
+    "svt_save_state": (ctypes.c_int, [_ctxp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "svt_load_state": (ctypes.c_int, [_ctxp, _vp, ctypes.c_size_t]),
+    "svt_kernel_launches": (ctypes.c_int64, [_ctxp]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsvt.so and declare every entry point.  Raises OSError if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise OSError("libsvt.so not found at %s: build it with paper_0810_3286_gb300.build.build() "
+                              "(there is no CPU fallback)" % path)
+            L = ctypes.CDLL(path)
+            for name, (res, args) in PROTOTYPES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class SVTError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status), message))

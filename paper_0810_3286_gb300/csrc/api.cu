@@ -1,0 +1,976 @@
+// C-ABI of libsvt: context, Omega storage build, the rank-adaptive block Lanczos shrink and the
+// loop of Algorithm 1 (Sec. 5.1.5).  Host code here only orchestrates: every arithmetic step on
+// the matrices runs in the kernels of omega.cu, sparse.cu and dense.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/svt.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace svt;
+
+namespace {
+
+constexpr int kBMax = 32;       // largest Lanczos block
+constexpr int kKMax = 96;       // largest projected problem (J b)
+constexpr int kMaxRankCap = 27; // s_k = r + 1 must leave >= 4 spare columns in a 32-wide block
+constexpr int kOversample = 4;  // block columns beyond the wanted triplets
+constexpr uint64_t kStateMagic = 0x5356545354415445ULL;  // "SVTSTATE"
+
+thread_local std::string g_create_error;
+
+// Temporary device buffers of one call, freed (after the stream drains) when the call returns.
+struct TmpBufs {
+  cudaStream_t st = nullptr;
+  std::vector<void*> ptrs;
+  explicit TmpBufs(cudaStream_t s) : st(s) {}
+  ~TmpBufs() {
+    if (ptrs.empty()) return;
+    cudaStreamSynchronize(st);
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  bool get(T** p, size_t count) {
+    void* v = nullptr;
+    if (cudaMalloc(&v, count ? count * sizeof(T) : 16) != cudaSuccess) {
+      (void)cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    ptrs.push_back(v);
+    *p = (T*)v;
+    return true;
+  }
+};
+
+}  // namespace
+
+struct svt_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  svt_options opt{};
+  int64_t m = 0, n = 0, nnz = 0;
+  int prec = SVT_FP64;
+  size_t vbytes = 8;
+  std::string last_error;
+  std::vector<void*> allocations;
+
+  // Omega
+  int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *row_idx = nullptr;
+  int32_t *csc_to_csr = nullptr, *csr_to_csc = nullptr;
+  void* Mv = nullptr;               // sampled entries, row-major order, value type
+  void* Ycsr[2] = {nullptr, nullptr};
+  void* Ycsc[2] = {nullptr, nullptr};
+  int ycur = 0;
+  double normF = 0.0;
+
+  // parameters / state of Algorithm 1
+  bool configured = false;
+  double tau = 0, delta = 0, eps = 1e-4;
+  int max_rank = 0;
+  int64_t k0 = 0, k = 0;
+  double norm2 = 0.0;
+  int r = 0;                        // rank of X^k
+  std::vector<double> d_host;       // sigma - tau of X^k
+  double* Ut = nullptr;             // m x kMaxRankCap+1: U diag(sigma - tau)
+  double* Uf = nullptr;             // m x cap: U (unscaled)
+  double* Vf = nullptr;             // n x cap: V
+  double* Vwarm = nullptr;          // n x kBMax warm start block
+  int warm_cols = 0;
+  uint64_t rng_counter = 0;
+
+  // Lanczos workspace
+  double *Ub = nullptr, *Vb = nullptr;   // block bases (blocks of rows x b)
+  double *T = nullptr, *S = nullptr, *theta = nullptr, *Xl = nullptr, *Wr = nullptr, *res = nullptr;
+  double *G = nullptr, *gpart = nullptr, *coef = nullptr, *coef2 = nullptr, *colnorm0 = nullptr;
+  double *Rinv = nullptr, *Rkeep = nullptr, *scale = nullptr, *apply_tmp = nullptr;
+  double *upd_partial = nullptr, *dscal = nullptr;
+  unsigned int* err = nullptr;
+  double* h_pin = nullptr;          // pinned host staging (theta, res, scalars)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // statistics of the last shrink
+  int last_cycles = 0, last_spmm = 0, last_s = 0, last_passes = 0;
+  double last_sigma1 = 0.0;
+  int64_t launches = 0;
+  int64_t total_spmm = 0, total_cycles = 0;
+};
+
+// ------------------------------------------------------------------------------------------------
+// helpers
+// ------------------------------------------------------------------------------------------------
+static svt_status fail(svt_ctx* c, svt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->last_error = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+#define CU(ctx, call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      (void)cudaGetLastError();                                                                \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? SVT_ERR_OOM : SVT_ERR_CUDA,         \
+                  "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                          \
+  } while (0)
+
+#define TRY(expr)                     \
+  do {                                \
+    svt_status s_ = (expr);           \
+    if (s_ != SVT_OK) return s_;      \
+  } while (0)
+
+static svt_status dalloc(svt_ctx* c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(c, SVT_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocations.push_back(*p);
+  return SVT_OK;
+}
+
+template <typename T>
+static svt_status dalloc_t(svt_ctx* c, T** p, size_t count) {
+  void* v = nullptr;
+  svt_status s = dalloc(c, &v, count * sizeof(T));
+  *p = (T*)v;
+  return s;
+}
+
+// Launch accounting + launch-error check.
+static svt_status launched(svt_ctx* c, int n) {
+  c->launches += n;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, SVT_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return SVT_OK;
+}
+
+static svt_status sync_and_check(svt_ctx* c) {
+  CU(c, cudaStreamSynchronize(c->st));
+  unsigned int e = 0;
+  CU(c, cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
+  if (e) {
+    CU(c, cudaMemset(c->err, 0, sizeof e));
+    if (e & SVT_DEVERR_INDEX_RANGE) return fail(c, SVT_ERR_ARG, "index outside [0,m) x [0,n)");
+    if (e & SVT_DEVERR_DUPLICATE) return fail(c, SVT_ERR_DUP_INDEX, "duplicate (row, col) pair in Omega");
+    if (e & SVT_DEVERR_NONFINITE) return fail(c, SVT_ERR_NUMERIC, "NaN or Inf in the residual");
+    if (e & SVT_DEVERR_CAPACITY) return fail(c, SVT_ERR_INTERNAL, "device buffer capacity exceeded");
+    if (e & SVT_DEVERR_JACOBI) return fail(c, SVT_ERR_NUMERIC, "projected Jacobi SVD did not converge");
+    // SVT_DEVERR_CHOL is informational (deflation handled in-kernel)
+  }
+  return SVT_OK;
+}
+
+static int choose_block(int s_need) {
+  int b = s_need + std::max(kOversample, s_need / 4);
+  b = (b + 7) / 8 * 8;
+  if (b > kBMax) b = kBMax;
+  if (b < 8) b = 8;
+  return b;
+}
+
+static uint64_t next_seed(svt_ctx* c) {
+  uint64_t z = c->opt.seed + (++c->rng_counter) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+static void* ycur_csr(svt_ctx* c) { return c->Ycsr[c->ycur]; }
+static void* ycur_csc(svt_ctx* c) { return c->Ycsc[c->ycur]; }
+
+// ------------------------------------------------------------------------------------------------
+// Block CGS2 + Cholesky QR of P (rows x b) against nq orthonormal blocks Q (stride q_stride).
+// Coefficients: P_in = Q (C1 + C2) + P_out (R2 R1); written to Tcol / Tdiag when given.
+// ------------------------------------------------------------------------------------------------
+static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long long q_stride, int nq, int rows, int b,
+                                 double* Tcol, double* Tdiag) {
+  int l = 0;
+  if (nq > 0) {
+    l += launch_gram(Q, q_stride, nq, P, rows, b, c->gpart, c->G, c->st);
+    l += launch_orth_small(0, c->G, nq, b, c->coef, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, nullptr, kKMax,
+                           nullptr, c->err, c->st);
+    l += launch_block_update(Q, q_stride, nq, c->coef, nullptr, P, rows, b, c->st);
+  }
+  l += launch_gram(Q, q_stride, nq, P, rows, b, c->gpart, c->G, c->st);
+  l += launch_orth_small(1, c->G, nq, b, c->coef, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, nullptr, kKMax, nullptr,
+                         c->err, c->st);
+  l += launch_block_update(Q, q_stride, nq, c->coef2, c->Rinv, P, rows, b, c->st);
+  l += launch_gram(nullptr, 0, 0, P, rows, b, c->gpart, c->G, c->st);
+  l += launch_orth_small(2, c->G, nq, b, nq > 0 ? c->coef : nullptr, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, Tcol,
+                         kKMax, Tdiag, c->err, c->st);
+  l += launch_block_update(nullptr, 0, 0, nullptr, c->Rinv, P, rows, b, c->st);
+  return launched(c, l);
+}
+
+// One block Golub-Kahan-Lanczos cycle with full reorthogonalisation from the start block in
+// Vb[0] (n x b).  On return theta/res (host, pinned) hold the Ritz values and residual estimates.
+static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h, const double** res_h) {
+  const int m = (int)c->m, n = (int)c->n;
+  const int K = J * b;
+  const long long su = (long long)m * b, sv = (long long)n * b;
+  CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
+  TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr));
+  int l = 0;
+  for (int j = 0; j < J; ++j) {
+    double* Uj = c->Ub + j * su;
+    double* Vj = c->Vb + j * sv;
+    l += launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, Uj, m, b, c->st);
+    TRY(launched(c, l)); l = 0;
+    TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b));
+    double* Vn = c->Vb + (j + 1) * sv;
+    l += launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, Vn, n, b, c->st);
+    TRY(launched(c, l)); l = 0;
+    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr));
+  }
+  // S is written with leading dimension kKMax by orth_small; the small SVD reads it as b x b with
+  // leading dimension b, so compact it first.
+  CU(c, cudaMemcpy2DAsync(c->Rkeep, b * sizeof(double), c->S, kKMax * sizeof(double), b * sizeof(double), b,
+                          cudaMemcpyDeviceToDevice, c->st));
+  const double tol_j = 1e-15;
+  l += launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err, c->st);
+  TRY(launched(c, l));
+  c->last_spmm += 2 * J;
+  c->total_spmm += 2 * J;
+  c->last_cycles += 1;
+  c->total_cycles += 1;
+  CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
+  TRY(sync_and_check(c));
+  *theta_h = c->h_pin;
+  *res_h = c->h_pin + kKMax;
+  return SVT_OK;
+}
+
+// Start block of the next cycle: the first `cols` right Ritz vectors V_basis Wr[:, 0:cols] (or the
+// warm-start block), random columns after them.
+static svt_status set_start_block(svt_ctx* c, int b, int warm) {
+  const int n = (int)c->n;
+  int l = 0;
+  if (warm > 0) {
+    // Vwarm is n x warm_cols (row-major, ld = warm_cols); copy the first `warm` columns into Vb[0] (ld b)
+    CU(c, cudaMemcpy2DAsync(c->Vb, b * sizeof(double), c->Vwarm, c->warm_cols * sizeof(double), warm * sizeof(double),
+                            n, cudaMemcpyDeviceToDevice, c->st));
+  }
+  if (warm < b) l += launch_random_block(c->Vb, n, b, warm, next_seed(c), c->st);
+  return launched(c, l);
+}
+
+// Keep the first `cols` right Ritz vectors of the last cycle (basis V_0..V_{J-1}) in Vwarm.
+static svt_status keep_ritz(svt_ctx* c, int b, int J, int cols) {
+  const int n = (int)c->n;
+  const int K = J * b;
+  cols = std::min(cols, std::min(K, kBMax));
+  int l = launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, cols, nullptr, c->Vwarm, c->st);
+  c->warm_cols = cols;
+  return launched(c, l);
+}
+
+// Rank-adaptive partial SVD of the current Y (Sec. 5.1.1).  Computes the leading singular triplets
+// until the rank policy stops: s = s_init; converge the first s triplets; while sigma_s > tau,
+// s += ell (reusing the converged Ritz vectors as the start block).  On return theta_out holds the
+// converged values (host), *s_out the final s, *K_out/J_out/b_out the last cycle's shape.
+static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<double>& theta_out, int* s_out,
+                              int* passes_out, int* b_out, int* J_out) {
+  const int kmin = (int)std::min(c->m, c->n);
+  const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-10 : 1e-6);
+  int s = std::min(s_init, kmin);
+  int passes = 1;
+  int b = choose_block(s);
+  int J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
+  c->last_cycles = 0;
+  c->last_spmm = 0;
+  int warm = std::min(c->warm_cols, b);
+  TRY(set_start_block(c, b, warm));
+  const int max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
+  for (int cyc = 0;; ++cyc) {
+    const double *th, *rs;
+    TRY(lanczos_cycle(c, b, J, &th, &rs));
+    const int K = J * b;
+    const int s_eff = std::min(s, K);
+    int conv = 0;
+    while (conv < s_eff && rs[conv] <= tol * th[0]) ++conv;
+    const bool all_conv = conv >= s_eff;
+    if (all_conv) {
+      const double last = th[s_eff - 1];
+      if (last > tau && s < kmin) {
+        if (s + c->opt.ell > kMaxRankCap + 1) {
+          theta_out.assign(th, th + s_eff);
+          *s_out = s;
+          return fail(c, SVT_ERR_RANK_LIMIT, "more than %d singular values exceed tau", kMaxRankCap);
+        }
+        s = std::min(s + c->opt.ell, kmin);
+        ++passes;
+        int nb = choose_block(s);
+        TRY(keep_ritz(c, b, J, std::min(b, nb)));
+        b = nb;
+        J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
+        TRY(set_start_block(c, b, std::min(c->warm_cols, b)));
+        continue;
+      }
+      theta_out.assign(th, th + s_eff);
+      *s_out = s_eff;
+      *passes_out = passes;
+      *b_out = b;
+      *J_out = J;
+      return SVT_OK;
+    }
+    if (cyc + 1 >= max_cycles)
+      return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
+                  max_cycles, conv, s_eff, rs[conv] / th[0]);
+    TRY(keep_ritz(c, b, J, b));
+    TRY(set_start_block(c, b, b));
+  }
+}
+
+// X = D_tau(Y): factors of the triplets with sigma > tau from the last cycle.
+static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out) {
+  std::vector<double> th;
+  int s = 0, passes = 0, b = 0, J = 0;
+  TRY(partial_svd(c, s_init, tau, th, &s, &passes, &b, &J));
+  int r = 0;
+  while (r < (int)th.size() && th[r] > tau) ++r;
+  if (r > c->max_rank) return fail(c, SVT_ERR_RANK_LIMIT, "rank %d exceeds max_rank %d", r, c->max_rank);
+  const int m = (int)c->m, n = (int)c->n;
+  const int K = J * b;
+  c->d_host.assign(r, 0.0);
+  for (int i = 0; i < r; ++i) c->d_host[i] = th[i] - tau;
+  c->last_s = s;
+  c->last_passes = passes;
+  c->last_sigma1 = th.empty() ? 0.0 : th[0];
+  int l = 0;
+  if (r > 0) {
+    std::memcpy(c->h_pin + 2 * kKMax, c->d_host.data(), sizeof(double) * r);
+    CU(c, cudaMemcpyAsync(c->scale, c->h_pin + 2 * kKMax, sizeof(double) * r, cudaMemcpyHostToDevice, c->st));
+    l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, nullptr, c->Uf, c->st);
+    l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, c->scale, c->Ut, c->st);
+    l += launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, r, nullptr, c->Vf, c->st);
+  }
+  TRY(launched(c, l));
+  // warm start of the next shrink: the leading right Ritz vectors
+  TRY(keep_ritz(c, b, J, std::min(b, std::max(r + c->opt.ell + 1, 8))));
+  c->r = r;
+  *r_out = r;
+  return SVT_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// C-ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" void svt_default_options(svt_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof *opt);
+  opt->precision = SVT_FP64;
+  opt->block = 0;
+  opt->ell = 5;
+  opt->k_max = 1000;
+  opt->lanczos_steps = 3;
+  opt->max_cycles = 40;
+  opt->lanczos_tol = 0.0;
+  opt->indices_on_device = 0;
+  opt->seed = 0x5eed5eedULL;
+  opt->stream = nullptr;
+}
+
+extern "C" const char* svt_last_error(const svt_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_create_error.c_str();
+}
+
+extern "C" int64_t svt_kernel_launches(const svt_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" void svt_destroy(svt_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocations) cudaFree(p);
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  delete c;
+}
+
+static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32_t* cols_d, const double* M_d) {
+  const int m = (int)c->m, n = (int)c->n;
+  const long long nnz = c->nnz;
+  int32_t *counts, *cursor, *scan_scratch, *src, *rows_csr, *maxseg;
+  const long long nmax = std::max<long long>(m, n) + 1;
+  TmpBufs tmp(c->st);
+  if (!tmp.get(&counts, nmax) || !tmp.get(&cursor, nmax) || !tmp.get(&scan_scratch, scan_scratch_ints(nmax)) ||
+      !tmp.get(&src, nnz) || !tmp.get(&rows_csr, nnz) || !tmp.get(&maxseg, 1))
+    return fail(c, SVT_ERR_OOM, "device allocation of build scratch failed");
+  int32_t* host_ptr = nullptr;
+  int l = 0;
+  // ---- CSR: major = row, minor = col, payload = input position
+  CU(c, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nmax, c->st));
+  CU(c, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nmax, c->st));
+  l += launch_count_major(rows_d, cols_d, nnz, m, n, counts, c->err, c->st);
+  l += launch_exclusive_scan(counts, c->row_ptr, m, scan_scratch, c->st);
+  l += launch_scatter_segments(rows_d, cols_d, nullptr, nnz, m, n, c->row_ptr, cursor, c->col_idx, src, c->st);
+  l += launch_sort_segments(c->row_ptr, m, c->col_idx, src, c->st);
+  l += launch_max_segment(c->row_ptr, m, maxseg, c->st);
+  TRY(launched(c, l)); l = 0;
+  TRY(sync_and_check(c));
+  int32_t mx = 0;
+  CU(c, cudaMemcpy(&mx, maxseg, sizeof mx, cudaMemcpyDeviceToHost));
+  if (mx > segment_smem_capacity()) {
+    host_ptr = new (std::nothrow) int32_t[m + 1];
+    if (!host_ptr) return fail(c, SVT_ERR_OOM, "host allocation failed");
+    CU(c, cudaMemcpy(host_ptr, c->row_ptr, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost));
+    int32_t* scratch = nullptr;
+    int L = 1;
+    while (L < mx) L <<= 1;
+    if (!tmp.get(&scratch, 2LL * L)) { delete[] host_ptr; return fail(c, SVT_ERR_OOM, "sort scratch"); }
+    for (int i = 0; i < m; ++i) {
+      int len = host_ptr[i + 1] - host_ptr[i];
+      if (len > segment_smem_capacity())
+        l += launch_sort_long_segment(c->col_idx + host_ptr[i], src + host_ptr[i], len, scratch, c->st);
+    }
+    delete[] host_ptr;
+    host_ptr = nullptr;
+    TRY(launched(c, l)); l = 0;
+  }
+  l += launch_check_duplicates(c->row_ptr, m, c->col_idx, c->err, c->st);
+  // values in row-major order
+  if (c->prec == SVT_FP64) l += launch_gather_f64(M_d, src, nnz, (double*)c->Mv, c->st);
+  else l += launch_gather_f64_to_f32(M_d, src, nnz, (float*)c->Mv, c->st);
+  l += launch_expand_ptr(c->row_ptr, m, rows_csr, c->st);
+  // ---- CSC: major = col, minor = row, payload = row-major position
+  CU(c, cudaMemsetAsync(counts, 0, sizeof(int32_t) * nmax, c->st));
+  CU(c, cudaMemsetAsync(cursor, 0, sizeof(int32_t) * nmax, c->st));
+  l += launch_count_major(c->col_idx, rows_csr, nnz, n, m, counts, c->err, c->st);
+  l += launch_exclusive_scan(counts, c->col_ptr, n, scan_scratch, c->st);
+  // payload: identity positions 0..nnz-1 (nullptr => p)
+  l += launch_scatter_segments(c->col_idx, rows_csr, nullptr, nnz, n, m, c->col_ptr, cursor, c->row_idx,
+                               c->csc_to_csr, c->st);
+  l += launch_sort_segments(c->col_ptr, n, c->row_idx, c->csc_to_csr, c->st);
+  l += launch_max_segment(c->col_ptr, n, maxseg, c->st);
+  TRY(launched(c, l)); l = 0;
+  TRY(sync_and_check(c));
+  CU(c, cudaMemcpy(&mx, maxseg, sizeof mx, cudaMemcpyDeviceToHost));
+  if (mx > segment_smem_capacity()) {
+    host_ptr = new (std::nothrow) int32_t[n + 1];
+    if (!host_ptr) return fail(c, SVT_ERR_OOM, "host allocation failed");
+    CU(c, cudaMemcpy(host_ptr, c->col_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+    int32_t* scratch = nullptr;
+    int L = 1;
+    while (L < mx) L <<= 1;
+    if (!tmp.get(&scratch, 2LL * L)) { delete[] host_ptr; return fail(c, SVT_ERR_OOM, "sort scratch"); }
+    for (int j = 0; j < n; ++j) {
+      int len = host_ptr[j + 1] - host_ptr[j];
+      if (len > segment_smem_capacity())
+        l += launch_sort_long_segment(c->row_idx + host_ptr[j], c->csc_to_csr + host_ptr[j], len, scratch, c->st);
+    }
+    delete[] host_ptr;
+    TRY(launched(c, l)); l = 0;
+  }
+  l += launch_invert_perm(c->csc_to_csr, nnz, c->csr_to_csc, c->st);
+  // ||P_Omega M||_F (float64, from the input values)
+  l += launch_sumsq_f64(M_d, nnz, c->upd_partial, c->dscal, c->st);
+  TRY(launched(c, l));
+  TRY(sync_and_check(c));
+  double ss = 0.0;
+  CU(c, cudaMemcpy(&ss, c->dscal, sizeof ss, cudaMemcpyDeviceToHost));
+  c->normF = std::sqrt(ss);
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
+                                 const double* M_omega, const svt_options* opt, svt_ctx** out) {
+  if (!out) return fail(nullptr, SVT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (m < 1 || n < 1 || m >= (1LL << 31) || n >= (1LL << 31))
+    return fail(nullptr, SVT_ERR_ARG, "dimensions must satisfy 1 <= m, n < 2^31");
+  if (nnz < 1 || nnz >= (1LL << 31) || nnz > m * n) return fail(nullptr, SVT_ERR_ARG, "need 1 <= nnz <= m*n, nnz < 2^31");
+  if (!rows || !cols || !M_omega) return fail(nullptr, SVT_ERR_ARG, "rows, cols and M_omega must be non-NULL");
+  svt_options o;
+  svt_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != SVT_FP64 && o.precision != SVT_FP32) return fail(nullptr, SVT_ERR_ARG, "unknown precision");
+  if (o.ell < 1) o.ell = 5;
+  if (o.k_max < 1) o.k_max = 1000;
+  if (o.lanczos_steps < 1) o.lanczos_steps = 3;
+  if (o.max_cycles < 1) o.max_cycles = 40;
+  svt_ctx* c = new (std::nothrow) svt_ctx();
+  if (!c) return fail(nullptr, SVT_ERR_OOM, "host allocation failed");
+  c->opt = o;
+  c->m = m; c->n = n; c->nnz = nnz;
+  c->prec = o.precision;
+  c->vbytes = c->prec == SVT_FP64 ? 8 : 4;
+  c->st = (cudaStream_t)o.stream;
+  auto bail = [&](svt_status s) {
+    g_create_error = c->last_error;
+    svt_destroy(c);
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    (void)cudaGetLastError();
+    fail(c, SVT_ERR_CUDA, "no CUDA device");
+    return bail(SVT_ERR_CUDA);
+  }
+  svt_status s = SVT_OK;
+#define A(expr) do { s = (expr); if (s != SVT_OK) return bail(s); } while (0)
+  A(dalloc_t(c, &c->err, 4));
+  if (cudaMemsetAsync(c->err, 0, 4, c->st) != cudaSuccess) { fail(c, SVT_ERR_CUDA, "memset"); return bail(SVT_ERR_CUDA); }
+  A(dalloc_t(c, &c->row_ptr, m + 1));
+  A(dalloc_t(c, &c->col_idx, nnz));
+  A(dalloc_t(c, &c->col_ptr, n + 1));
+  A(dalloc_t(c, &c->row_idx, nnz));
+  A(dalloc_t(c, &c->csc_to_csr, nnz));
+  A(dalloc_t(c, &c->csr_to_csc, nnz));
+  A(dalloc(c, &c->Mv, nnz * c->vbytes));
+  for (int i = 0; i < 2; ++i) {
+    A(dalloc(c, &c->Ycsr[i], nnz * c->vbytes));
+    A(dalloc(c, &c->Ycsc[i], nnz * c->vbytes));
+  }
+  const int cap = kMaxRankCap + 1;
+  A(dalloc_t(c, &c->Ut, (size_t)m * cap));
+  A(dalloc_t(c, &c->Uf, (size_t)m * cap));
+  A(dalloc_t(c, &c->Vf, (size_t)n * cap));
+  A(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
+  A(dalloc_t(c, &c->Ub, (size_t)m * (kKMax + kBMax)));
+  A(dalloc_t(c, &c->Vb, (size_t)n * (kKMax + kBMax)));
+  A(dalloc_t(c, &c->T, (size_t)kKMax * kKMax));
+  A(dalloc_t(c, &c->S, (size_t)kKMax * kBMax));
+  A(dalloc_t(c, &c->theta, kKMax));
+  A(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
+  A(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
+  A(dalloc_t(c, &c->res, kKMax));
+  A(dalloc_t(c, &c->G, 128 * 32));
+  // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
+  A(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
+  A(dalloc_t(c, &c->coef, (size_t)kKMax * kBMax));
+  A(dalloc_t(c, &c->coef2, (size_t)kKMax * kBMax));
+  A(dalloc_t(c, &c->colnorm0, kBMax));
+  A(dalloc_t(c, &c->Rinv, kBMax * kBMax));
+  A(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
+  A(dalloc_t(c, &c->scale, 64));
+  A(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
+  A(dalloc_t(c, &c->dscal, 16));
+  if (cudaMallocHost((void**)&c->h_pin, sizeof(double) * 4 * kKMax) != cudaSuccess) {
+    (void)cudaGetLastError();
+    fail(c, SVT_ERR_OOM, "cudaMallocHost failed");
+    return bail(SVT_ERR_OOM);
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    (void)cudaGetLastError();
+    fail(c, SVT_ERR_CUDA, "cudaEventCreate failed");
+    return bail(SVT_ERR_CUDA);
+  }
+  // inputs on the device
+  const int32_t *rows_d = rows, *cols_d = cols;
+  const double* M_d = M_omega;
+  TmpBufs staged(c->st);
+  if (!o.indices_on_device) {
+    int32_t *r2, *c2;
+    double* m2;
+    if (!staged.get(&r2, nnz) || !staged.get(&c2, nnz) || !staged.get(&m2, nnz)) {
+      fail(c, SVT_ERR_OOM, "device allocation of the input copy failed");
+      return bail(SVT_ERR_OOM);
+    }
+    if (cudaMemcpyAsync(r2, rows, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(c2, cols, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
+        cudaMemcpyAsync(m2, M_omega, sizeof(double) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      fail(c, SVT_ERR_CUDA, "host-to-device copy of Omega failed");
+      return bail(SVT_ERR_CUDA);
+    }
+    rows_d = r2; cols_d = c2; M_d = m2;
+  }
+  A(build_structure(c, rows_d, cols_d, M_d));
+  // Y^0 = 0 until configured
+  if (cudaMemsetAsync(c->Ycsr[0], 0, nnz * c->vbytes, c->st) != cudaSuccess ||
+      cudaMemsetAsync(c->Ycsc[0], 0, nnz * c->vbytes, c->st) != cudaSuccess) {
+    fail(c, SVT_ERR_CUDA, "memset failed");
+    return bail(SVT_ERR_CUDA);
+  }
+  A(sync_and_check(c));
+#undef A
+  *out = c;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double eps, int max_rank, int64_t k0) {
+  if (!c) return SVT_ERR_ARG;
+  if (max_rank < 1 || max_rank > kMaxRankCap)
+    return fail(c, SVT_ERR_ARG, "max_rank must be in [1, %d]", kMaxRankCap);
+  const double mn = (double)c->m * (double)c->n;
+  c->tau = tau > 0 ? tau : 5.0 * std::sqrt(mn);
+  c->delta = delta > 0 ? delta : 1.2 * mn / (double)c->nnz;
+  c->eps = eps > 0 ? eps : 1e-4;
+  c->max_rank = max_rank;
+  if (!std::isfinite(c->tau) || !std::isfinite(c->delta)) return fail(c, SVT_ERR_ARG, "tau/delta not finite");
+  // ||P_Omega M||_2: leading singular value of Y = P_Omega M (Lanczos, s = 1)
+  c->ycur = 0;
+  c->warm_cols = 0;
+  TRY(launched(c, launch_scale_values(c->prec, c->Mv, 1.0, c->Ycsr[0], c->Ycsc[0], c->csr_to_csc, c->nnz, c->st)));
+  std::vector<double> th;
+  int s = 0, passes = 0, b = 0, J = 0;
+  // huge tau so that the rank policy stops after the first converged triplet
+  TRY(partial_svd(c, 1, INFINITY, th, &s, &passes, &b, &J));
+  c->norm2 = th.empty() ? 0.0 : th[0];
+  if (!(c->norm2 > 0.0)) return fail(c, SVT_ERR_NUMERIC, "||P_Omega M||_2 is zero");
+  TRY(keep_ritz(c, b, J, std::min(b, 8)));
+  if (k0 >= 0) c->k0 = k0;
+  else c->k0 = (int64_t)std::ceil(c->tau / (c->delta * c->norm2));
+  TRY(launched(c, launch_scale_values(c->prec, c->Mv, (double)c->k0 * c->delta, c->Ycsr[0], c->Ycsc[0],
+                                      c->csr_to_csc, c->nnz, c->st)));
+  c->r = 0;
+  c->k = 0;
+  c->d_host.clear();
+  c->configured = true;
+  return sync_and_check(c);
+}
+
+extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
+  if (!c) return SVT_ERR_ARG;
+  if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
+  CU(c, cudaEventRecord(c->ev0, c->st));
+  int r = 0;
+  TRY(shrink_current(c, c->tau, c->r + 1, &r));
+  const int nxt = 1 - c->ycur;
+  TRY(launched(c, launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
+                                      c->Ycsc[nxt], c->Ut, c->Vf, r, (int)c->m, c->delta, c->upd_partial, c->dscal,
+                                      c->err, c->st)));
+  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaEventRecord(c->ev1, c->st));
+  TRY(sync_and_check(c));
+  const double res = std::sqrt(c->h_pin[3 * kKMax]) / c->normF;
+  c->k += 1;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  if (info) {
+    info->k = c->k;
+    info->r = r;
+    info->s = c->last_s;
+    info->passes = c->last_passes;
+    info->lanczos_cycles = c->last_cycles;
+    info->spmm_calls = c->last_spmm;
+    info->residual = res;
+    info->sigma1 = c->last_sigma1;
+    info->ms = ms;
+  }
+  if (!std::isfinite(res)) return fail(c, SVT_ERR_NUMERIC, "residual is not finite");
+  if (res <= c->eps) return SVT_STOPPED;
+  c->ycur = nxt;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_solve(svt_ctx* c, double tau, double delta, double eps, int max_rank, svt_result* out) {
+  if (!c) return SVT_ERR_ARG;
+  cudaEvent_t e0, e1;
+  CU(c, cudaEventCreate(&e0));
+  CU(c, cudaEventCreate(&e1));
+  CU(c, cudaEventRecord(e0, c->st));
+  const int64_t spmm0 = c->total_spmm, cyc0 = c->total_cycles;
+  svt_status s = svt_configure(c, tau, delta, eps, max_rank, -1);
+  svt_step_info info{};
+  info.residual = INFINITY;
+  bool converged = false;
+  if (s == SVT_OK) {
+    for (int it = 0; it < c->opt.k_max; ++it) {
+      s = svt_step(c, &info);
+      if (s == SVT_STOPPED) { converged = true; s = SVT_OK; break; }
+      if (s != SVT_OK) break;
+    }
+    if (s == SVT_OK && !converged) s = fail(c, SVT_ERR_NOT_CONVERGED, "k_max iterations reached");
+  }
+  cudaEventRecord(e1, c->st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out) {
+    out->iterations = c->k;
+    out->k0 = c->k0;
+    out->rank = c->r;
+    out->converged = converged ? 1 : 0;
+    out->residual = info.residual;
+    out->norm2_M = c->norm2;
+    out->normF_M = c->normF;
+    out->ms = ms;
+    out->spmm_calls = c->total_spmm - spmm0;
+    out->lanczos_cycles = c->total_cycles - cyc0;
+  }
+  return s;
+}
+
+extern "C" svt_status svt_get_rank(const svt_ctx* c, int* r) {
+  if (!c || !r) return SVT_ERR_ARG;
+  *r = c->r;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_get_factors(svt_ctx* c, double* U, double* d, double* V, int capacity_r) {
+  if (!c) return SVT_ERR_ARG;
+  if (capacity_r < c->r) return fail(c, SVT_ERR_ARG, "capacity_r %d < rank %d", capacity_r, c->r);
+  const int r = c->r;
+  if (r == 0) return SVT_OK;
+  if (U)
+    CU(c, cudaMemcpy2DAsync(U, sizeof(double) * capacity_r, c->Uf, sizeof(double) * r, sizeof(double) * r, c->m,
+                            cudaMemcpyDeviceToHost, c->st));
+  if (V)
+    CU(c, cudaMemcpy2DAsync(V, sizeof(double) * capacity_r, c->Vf, sizeof(double) * r, sizeof(double) * r, c->n,
+                            cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
+  if (d) std::memcpy(d, c->d_host.data(), sizeof(double) * r);
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_get_Y(svt_ctx* c, double* y) {
+  if (!c || !y) return SVT_ERR_ARG;
+  double* tmp = nullptr;
+  TRY(dalloc_t(c, &tmp, c->nnz));
+  TRY(launched(c, launch_store_values(c->prec, ycur_csr(c), tmp, c->nnz, c->st)));
+  CU(c, cudaMemcpyAsync(y, tmp, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
+  c->allocations.pop_back();
+  cudaFree(tmp);
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_set_Y(svt_ctx* c, const double* y) {
+  if (!c || !y) return SVT_ERR_ARG;
+  double* tmp = nullptr;
+  TRY(dalloc_t(c, &tmp, c->nnz));
+  CU(c, cudaMemcpyAsync(tmp, y, sizeof(double) * c->nnz, cudaMemcpyHostToDevice, c->st));
+  TRY(launched(c, launch_load_values(c->prec, tmp, ycur_csr(c), ycur_csc(c), c->csr_to_csc, c->nnz, c->st)));
+  CU(c, cudaStreamSynchronize(c->st));
+  c->allocations.pop_back();
+  cudaFree(tmp);
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_get_structure(svt_ctx* c, int32_t* row_ptr, int32_t* col_idx, int32_t* col_ptr,
+                                        int32_t* row_idx, int32_t* csc_to_csr) {
+  if (!c) return SVT_ERR_ARG;
+  if (row_ptr) CU(c, cudaMemcpyAsync(row_ptr, c->row_ptr, 4 * (c->m + 1), cudaMemcpyDeviceToHost, c->st));
+  if (col_idx) CU(c, cudaMemcpyAsync(col_idx, c->col_idx, 4 * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  if (col_ptr) CU(c, cudaMemcpyAsync(col_ptr, c->col_ptr, 4 * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
+  if (row_idx) CU(c, cudaMemcpyAsync(row_idx, c->row_idx, 4 * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  if (csc_to_csr) CU(c, cudaMemcpyAsync(csc_to_csr, c->csc_to_csr, 4 * c->nnz, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_shrink(svt_ctx* c, double tau, int* r_out, double* sigma) {
+  if (!c) return SVT_ERR_ARG;
+  if (tau <= 0) tau = c->tau;
+  if (!(tau > 0)) return fail(c, SVT_ERR_ARG, "tau must be positive (or configured)");
+  if (c->max_rank < 1) c->max_rank = kMaxRankCap;
+  int r = 0;
+  TRY(shrink_current(c, tau, c->r + 1, &r));
+  TRY(sync_and_check(c));
+  if (r_out) *r_out = r;
+  if (sigma)
+    for (int i = 0; i < r; ++i) sigma[i] = c->d_host[i] + tau;
+  return SVT_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+extern "C" svt_status svt_apply_Y(svt_ctx* c, const double* V, int b, double* W) {
+  if (!c || !V || !W) return SVT_ERR_ARG;
+  if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
+  if (!aligned16(V) || !aligned16(W)) return fail(c, SVT_ERR_ARG, "V and W must be 16-byte aligned");
+  TRY(launched(c, launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), V, W, (int)c->m, b, c->st)));
+  return sync_and_check(c);
+}
+
+extern "C" svt_status svt_apply_Yt(svt_ctx* c, const double* U, int b, double* Z) {
+  if (!c || !U || !Z) return SVT_ERR_ARG;
+  if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
+  if (!aligned16(U) || !aligned16(Z)) return fail(c, SVT_ERR_ARG, "U and Z must be 16-byte aligned");
+  TRY(launched(c, launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), U, Z, (int)c->n, b, c->st)));
+  return sync_and_check(c);
+}
+
+extern "C" svt_status svt_sddmm_update(svt_ctx* c, const double* Ut, const double* V, int r, double delta,
+                                       const double* y_in, double* y_out, double* res2) {
+  if (!c || !y_in || !y_out || !res2) return SVT_ERR_ARG;
+  if (r < 0 || r > 64 || (r > 0 && (!Ut || !V))) return fail(c, SVT_ERR_ARG, "need 0 <= r <= 64 and factors");
+  // the kernel works in the context's value type: stage float64 in/out through the Y buffers
+  const int nxt = 1 - c->ycur;
+  TRY(launched(c, launch_load_values(c->prec, y_in, c->Ycsr[nxt], nullptr, nullptr, c->nnz, c->st)));
+  TRY(launched(c, launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, c->Ycsr[nxt],
+                                      c->Ycsc[nxt], nullptr, Ut, V, r, (int)c->m, delta, c->upd_partial, c->dscal,
+                                      c->err, c->st)));
+  TRY(launched(c, launch_store_values(c->prec, c->Ycsc[nxt], y_out, c->nnz, c->st)));
+  CU(c, cudaMemcpyAsync(res2, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return sync_and_check(c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Omega sampler
+// ------------------------------------------------------------------------------------------------
+extern "C" svt_status svt_sample_omega(int64_t m, int64_t n, int64_t nnz, uint64_t seed, int32_t* rows,
+                                       int32_t* cols, void* stream) {
+  if (m < 1 || n < 1 || m >= (1LL << 31) || n >= (1LL << 31)) return fail(nullptr, SVT_ERR_ARG, "bad dimensions");
+  const long long N = m * n;
+  if (nnz < 0 || nnz > N || nnz >= (1LL << 31)) return fail(nullptr, SVT_ERR_ARG, "need 0 <= nnz <= m*n");
+  if (nnz > 0 && (!rows || !cols)) return fail(nullptr, SVT_ERR_ARG, "rows/cols are NULL");
+  if (nnz == 0) return SVT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<void*> bufs;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : bufs) cudaFree(p);
+  };
+  auto mal = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+    bufs.push_back(*p);
+    return true;
+  };
+  double margin = 8.0;
+  for (int attempt = 0; attempt < 6; ++attempt, margin *= 2.0) {
+    const double want = (double)nnz + margin * std::sqrt((double)nnz) + 64.0;
+    uint64_t thresh;
+    long long cap;
+    if (want >= (double)N) {
+      thresh = ~0ULL;
+      cap = N;
+    } else {
+      double frac = want / (double)N;
+      thresh = (uint64_t)(frac * 18446744073709551616.0);
+      cap = (long long)(want + margin * std::sqrt(want) + 64.0);
+      if (cap > N) cap = N;
+    }
+    unsigned long long *ck = nullptr, *cid = nullptr, *cnt = nullptr;
+    void* state = nullptr;
+    if (!mal((void**)&ck, sizeof(unsigned long long) * cap) || !mal((void**)&cid, sizeof(unsigned long long) * cap) ||
+        !mal((void**)&cnt, sizeof(unsigned long long)) || !mal(&state, (size_t)omega_select_state_bytes())) {
+      cleanup();
+      return fail(nullptr, SVT_ERR_OOM, "device allocation failed in svt_sample_omega");
+    }
+    launch_omega_filter(seed, N, thresh, ck, cid, cap, cnt, st);
+    unsigned long long count = 0;
+    if (cudaMemcpyAsync(&count, cnt, sizeof count, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      cleanup();
+      return fail(nullptr, SVT_ERR_CUDA, "svt_sample_omega: filter failed");
+    }
+    if ((long long)count < nnz || (long long)count > cap) {
+      // too few candidates (threshold too low) or overflow: retry with a wider margin
+      cleanup();
+      bufs.clear();
+      if ((long long)count > cap) margin = std::max(1.0, margin / 4.0);
+      continue;
+    }
+    launch_omega_select(ck, cid, cnt, nnz, state, st);
+    const long long nb = omega_compact_blocks(N);
+    int32_t *bc = nullptr, *bo = nullptr, *scr = nullptr;
+    unsigned int* err = nullptr;
+    if (!mal((void**)&bc, sizeof(int32_t) * nb) || !mal((void**)&bo, sizeof(int32_t) * (nb + 1)) ||
+        !mal((void**)&scr, sizeof(int32_t) * scan_scratch_ints(nb)) || !mal((void**)&err, sizeof(unsigned int))) {
+      cleanup();
+      return fail(nullptr, SVT_ERR_OOM, "device allocation failed in svt_sample_omega");
+    }
+    cudaMemsetAsync(err, 0, sizeof(unsigned int), st);
+    launch_omega_compact(seed, N, n, state, bc, bo, scr, rows, cols, nnz, err, st);
+    unsigned int e = 0;
+    int32_t total = 0;
+    cudaMemcpyAsync(&e, err, sizeof e, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&total, bo + nb, sizeof total, cudaMemcpyDeviceToHost, st);
+    cudaError_t ce = cudaStreamSynchronize(st);
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    cleanup();
+    if (ce != cudaSuccess) return fail(nullptr, SVT_ERR_CUDA, "svt_sample_omega: %s", cudaGetErrorString(ce));
+    if (e || total != nnz) return fail(nullptr, SVT_ERR_INTERNAL, "svt_sample_omega: selected %d of %lld", total,
+                                       (long long)nnz);
+    return SVT_OK;
+  }
+  return fail(nullptr, SVT_ERR_INTERNAL, "svt_sample_omega: threshold search failed");
+}
+
+// ------------------------------------------------------------------------------------------------
+// Checkpoint / resume
+// ------------------------------------------------------------------------------------------------
+struct StateHeader {
+  uint64_t magic;
+  int64_t m, n, nnz;
+  int32_t prec, r, warm_cols, configured;
+  int64_t k0, k;
+  double tau, delta, eps, norm2;
+  int32_t max_rank, ycur_unused;
+  uint64_t rng_counter;
+};
+
+static size_t state_bytes(const svt_ctx* c) {
+  return sizeof(StateHeader) + c->nnz * c->vbytes + sizeof(double) * (size_t)c->r * (1 + c->m + c->m + c->n) +
+         sizeof(double) * (size_t)c->n * c->warm_cols;
+}
+
+extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
+  if (!c || !bytes) return SVT_ERR_ARG;
+  const size_t need = state_bytes(c);
+  if (!buf) { *bytes = need; return SVT_OK; }
+  if (*bytes < need) return fail(c, SVT_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
+  StateHeader h{};
+  h.magic = kStateMagic; h.m = c->m; h.n = c->n; h.nnz = c->nnz; h.prec = c->prec; h.r = c->r;
+  h.warm_cols = c->warm_cols; h.configured = c->configured; h.k0 = c->k0; h.k = c->k; h.tau = c->tau;
+  h.delta = c->delta; h.eps = c->eps; h.norm2 = c->norm2; h.max_rank = c->max_rank; h.rng_counter = c->rng_counter;
+  char* p = (char*)buf;
+  std::memcpy(p, &h, sizeof h); p += sizeof h;
+  CU(c, cudaMemcpyAsync(p, ycur_csr(c), c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st)); p += c->nnz * c->vbytes;
+  std::memcpy(p, c->d_host.data(), sizeof(double) * c->r); p += sizeof(double) * c->r;
+  CU(c, cudaMemcpyAsync(p, c->Ut, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->m * c->r;
+  CU(c, cudaMemcpyAsync(p, c->Uf, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->m * c->r;
+  CU(c, cudaMemcpyAsync(p, c->Vf, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->n * c->r;
+  CU(c, cudaMemcpyAsync(p, c->Vwarm, sizeof(double) * c->n * c->warm_cols, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
+  *bytes = need;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return SVT_ERR_ARG;
+  if (bytes < sizeof(StateHeader)) return fail(c, SVT_ERR_ARG, "state buffer too small");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  if (h.magic != kStateMagic || h.m != c->m || h.n != c->n || h.nnz != c->nnz || h.prec != c->prec)
+    return fail(c, SVT_ERR_ARG, "state does not match this context");
+  if (h.r < 0 || h.r > kMaxRankCap || h.warm_cols < 0 || h.warm_cols > kBMax)
+    return fail(c, SVT_ERR_ARG, "corrupt state");
+  c->r = h.r; c->warm_cols = h.warm_cols; c->configured = h.configured != 0; c->k0 = h.k0; c->k = h.k;
+  c->tau = h.tau; c->delta = h.delta; c->eps = h.eps; c->norm2 = h.norm2; c->max_rank = h.max_rank;
+  c->rng_counter = h.rng_counter;
+  if (bytes < state_bytes(c)) return fail(c, SVT_ERR_ARG, "state buffer too small");
+  const char* p = (const char*)buf + sizeof h;
+  CU(c, cudaMemcpyAsync(ycur_csr(c), p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st)); p += c->nnz * c->vbytes;
+  c->d_host.assign((const double*)p, (const double*)p + c->r); p += sizeof(double) * c->r;
+  CU(c, cudaMemcpyAsync(c->Ut, p, sizeof(double) * c->m * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->m * c->r;
+  CU(c, cudaMemcpyAsync(c->Uf, p, sizeof(double) * c->m * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->m * c->r;
+  CU(c, cudaMemcpyAsync(c->Vf, p, sizeof(double) * c->n * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->n * c->r;
+  CU(c, cudaMemcpyAsync(c->Vwarm, p, sizeof(double) * c->n * c->warm_cols, cudaMemcpyHostToDevice, c->st));
+  // rebuild the column-major copy of Y from the row-major values
+  if (c->prec == SVT_FP64)
+    TRY(launched(c, launch_gather_f64((const double*)ycur_csr(c), c->csc_to_csr, c->nnz, (double*)ycur_csc(c), c->st)));
+  else {
+    double* tmp = nullptr;
+    TRY(dalloc_t(c, &tmp, c->nnz));
+    TRY(launched(c, launch_store_values(c->prec, ycur_csr(c), tmp, c->nnz, c->st)));
+    TRY(launched(c, launch_gather_f64_to_f32(tmp, c->csc_to_csr, c->nnz, (float*)ycur_csc(c), c->st)));
+    CU(c, cudaStreamSynchronize(c->st));
+    c->allocations.pop_back();
+    cudaFree(tmp);
+  }
+  return sync_and_check(c);
+}

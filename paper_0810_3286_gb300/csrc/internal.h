@@ -1,0 +1,114 @@
+// Internal launch interface between the C-ABI layer (api.cu) and the kernels.
+// Every launcher issues its kernels on `st` and returns the number of kernels launched; they
+// never synchronise.  Pointers are device pointers unless the name says otherwise.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace svt {
+
+// ----- generic ------------------------------------------------------------------------------
+// out[0..n] = exclusive prefix sum of in[0..n-1], out[n] = total.  Needs scan_scratch_ints(n) ints.
+long long scan_scratch_ints(long long n);
+int launch_exclusive_scan(const int32_t* in, int32_t* out, long long n, int32_t* scratch, cudaStream_t st);
+
+// ----- Omega storage (sorted segments) ----------------------------------------------------------
+// Counts of `major` keys; flags out-of-range pairs (major >= n_major or minor >= n_minor).
+int launch_count_major(const int32_t* major, const int32_t* minor, long long nnz, int n_major, int n_minor,
+                       int32_t* counts, unsigned int* err, cudaStream_t st);
+// Scatter (minor, payload) into segments of `ptr` (cursor must be zeroed).
+int launch_scatter_segments(const int32_t* major, const int32_t* minor, const int32_t* payload, long long nnz,
+                            int n_major, int n_minor, const int32_t* ptr, int32_t* cursor, int32_t* out_minor,
+                            int32_t* out_payload, cudaStream_t st);
+// Sort every segment [ptr[s], ptr[s+1]) with length <= seg_cap by minor key (carrying payload),
+// in shared memory.  Longer segments are left for launch_sort_long_segment.
+int segment_smem_capacity();
+int launch_sort_segments(const int32_t* ptr, int n_seg, int32_t* minor, int32_t* payload, cudaStream_t st);
+// Sort one long segment in global memory (scratch: 2 * pow2(len) ints).
+int launch_sort_long_segment(int32_t* minor, int32_t* payload, int len, int32_t* scratch, cudaStream_t st);
+// Longest segment length -> *out (device int).
+int launch_max_segment(const int32_t* ptr, int n_seg, int32_t* out, cudaStream_t st);
+// Flags adjacent equal minor keys inside a segment (duplicate pairs).
+int launch_check_duplicates(const int32_t* ptr, int n_seg, const int32_t* minor, unsigned int* err, cudaStream_t st);
+// major index of every position (expand ptr): out[p] = s for ptr[s] <= p < ptr[s+1].
+int launch_expand_ptr(const int32_t* ptr, int n_seg, int32_t* out, cudaStream_t st);
+// out[i] = in[perm[i]] for float64 input, written as double or float.
+int launch_gather_f64(const double* in, const int32_t* perm, long long n, double* out, cudaStream_t st);
+int launch_gather_f64_to_f32(const double* in, const int32_t* perm, long long n, float* out, cudaStream_t st);
+// inv[perm[i]] = i
+int launch_invert_perm(const int32_t* perm, long long n, int32_t* inv, cudaStream_t st);
+// *out = sum of squares of x (float64, deterministic two-stage); partial needs 1024 doubles.
+int launch_sumsq_f64(const double* x, long long n, double* partial, double* out, cudaStream_t st);
+
+// ----- Omega sampler ---------------------------------------------------------------------------
+struct SelectState;  // device-side radix-select state
+long long omega_select_state_bytes();
+int launch_omega_filter(uint64_t seed, long long N, uint64_t thresh, unsigned long long* cand_key,
+                        unsigned long long* cand_id, long long cap, unsigned long long* count, cudaStream_t st);
+int launch_omega_select(const unsigned long long* cand_key, const unsigned long long* cand_id,
+                        const unsigned long long* count, long long rank, void* state, cudaStream_t st);
+long long omega_compact_blocks(long long N);
+int launch_omega_compact(uint64_t seed, long long N, long long n_cols, const void* state, int32_t* block_counts,
+                         int32_t* block_offsets, int32_t* scan_scratch, int32_t* rows, int32_t* cols,
+                         long long m, unsigned int* err, cudaStream_t st);
+
+// ----- per-iteration kernels -------------------------------------------------------------------
+// Out (n_out x b) = S X with S given in compressed segments (ptr, idx, val) and X (n_in x b).
+// precision 0: float64 values and accumulation; 1: float32 values and accumulation.
+int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
+                double* Out, int n_out, int b, cudaStream_t st);
+
+// Gram of a tall block against a basis: G ((nq+1) b x b) = [Q_0 .. Q_{nq-1}, P]^T P, where the Q_i
+// are n x b blocks spaced `q_stride` doubles apart.  partial: gram_partial_doubles(...) doubles.
+long long gram_partial_doubles(int n, int nq, int b);
+int launch_gram(const double* Q, long long q_stride, int nq, const double* P, int n, int b, double* partial,
+                double* G, cudaStream_t st);
+
+// P <- (P - Q C) Rinv  (C: nq b x b; Rinv: b x b upper triangular, or NULL = identity)
+int launch_block_update(const double* Q, long long q_stride, int nq, const double* C, const double* Rinv,
+                        double* P, int n, int b, cudaStream_t st);
+
+// Small-matrix step of block CGS2 + Cholesky QR.  See lanczos_orth_step in kernels.cu.
+// mode 0: first pass.  In: G1 = [Q,P]^T P (before projection).  Writes C1 (coefficients,
+//         nq b x b) to coef, keeps ||p_c||^2 in colnorm0.
+// mode 1: after P -= Q C1.  In: G2 = [Q,P]^T P.  Writes C2 to coef2, R1 = chol(P^T P - C2^T C2)
+//         (deflating columns whose norm fell below sqrt(eps) of colnorm0) and Rinv1.
+// mode 2: after P <- (P - Q C2) Rinv1.  In: G3 = P^T P.  R2 = chol(G3), Rinv2, and the final
+//         coefficient block: Tcol[0..nq b) = C1 + C2, diag block R2 R1 into Tdiag.
+int launch_orth_small(int mode, const double* G, int nq, int b, double* coef, double* coef2, double* colnorm0,
+                      double* Rinv, double* Rkeep, double* Tcol, int ldT, double* Tdiag, unsigned int* err,
+                      cudaStream_t st);
+
+// Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT): T = Xl diag(theta) Wr^T,
+// theta decreasing; Xl, Wr written K x K row-major.  Also res[i] = || S (Xl rows [K-b, K), column i) ||
+// for the b x b block S (upper triangular, may be NULL -> res = 0).
+int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl, double* Wr,
+                     double* res, double tol, int max_sweeps, unsigned int* err, cudaStream_t st);
+
+// Out (n x s) = sum over blocks i of B_i (n x b) W[i b .. i b + b, 0 .. s) , columns scaled by
+// scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).
+int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
+                         const double* scale, double* Out, cudaStream_t st);
+
+// Fill an n x b block with uniform(-1, 1) numbers from SplitMix64 (columns c >= c0 only).
+int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStream_t st);
+
+// Fused X-on-Omega + dual step + residual (precision 0: float64 values, 1: float32 values):
+//   x_p = sum_t Ut[i,t] V[j,t];  e = M_p - x_p;  y_out[p] = y_in[p] + delta e;
+//   y_out_csc[csr_to_csc[p]] = y_out[p] (if y_out_csc);  res2 = sum e^2 (deterministic).
+int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
+                        const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
+                        const double* V, int r, int n_rows, double delta, double* partial, double* res2,
+                        unsigned int* err, cudaStream_t st);
+int sddmm_partial_doubles();
+
+// y[p] = alpha * M[p] for the value type of `precision`; also writes the CSC copy via csr_to_csc.
+int launch_scale_values(int precision, const void* M, double alpha, void* y, void* y_csc, const int32_t* csr_to_csc,
+                        long long nnz, cudaStream_t st);
+// Copy float64 values (row-major order) into the value type, plus CSC copy.
+int launch_load_values(int precision, const double* src, void* y, void* y_csc, const int32_t* csr_to_csc,
+                       long long nnz, cudaStream_t st);
+// Store the value type (row-major order) as float64.
+int launch_store_values(int precision, const void* y, double* dst, long long nnz, cudaStream_t st);
+
+}  // namespace svt

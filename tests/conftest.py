@@ -21,3 +21,15 @@ def oracle_c1_run():
     p = config_problem("plain_fp64_200", 0)
     res = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default())
     return p, res
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    """Builds libsvt (if needed) and returns torch with cuda:0 selected."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is visible")
+    from paper_0810_3286_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch

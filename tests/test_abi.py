@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every entry point that include/svt.h declares (no GPU
+work: nothing here launches a kernel).  Also checks the binding's prototypes cover the header."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "svt.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(svt_[a-z_A-Z0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_0810_3286_gb300 import build
+    return build.build()
+
+
+def test_header_declares_expected_calls():
+    names = _declared()
+    for required in ["svt_create", "svt_step", "svt_solve", "svt_get_factors", "svt_configure", "svt_destroy",
+                     "svt_get_Y", "svt_save_state", "svt_load_state", "svt_sample_omega", "svt_last_error"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(svt_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_covers_header(libpath):
+    from paper_0810_3286_gb300 import _abi
+    L = _abi.load(libpath)
+    for name in _declared():
+        assert hasattr(L, name)
+        assert name in _abi.PROTOTYPES, name
+    # host-only calls that do not touch the GPU
+    import ctypes
+    opt = _abi.svt_options()
+    L.svt_default_options(ctypes.byref(opt))
+    assert opt.ell == 5 and opt.k_max == 1000 and opt.precision == _abi.SVT_FP64
+    assert L.svt_kernel_launches(None) == 0
+
+
+def test_create_rejects_bad_arguments_before_any_device_work(libpath):
+    """Argument validation happens on the host before the library touches a device."""
+    import ctypes
+    import numpy as np
+    from paper_0810_3286_gb300 import _abi
+    L = _abi.load(libpath)
+    rows = np.zeros(3, np.int32)
+    ctx = ctypes.c_void_p()
+    st = L.svt_create(0, 5, 3, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, None, ctypes.byref(ctx))
+    assert st == _abi.SVT_ERR_ARG and not ctx.value
+    st = L.svt_create(4, 5, 21, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, None, ctypes.byref(ctx))
+    assert st == _abi.SVT_ERR_ARG
+    assert b"nnz" in L.svt_last_error(None)
