@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the SVT hot path on GB300: one step = one complete matrix-completion solve.
+
+Workload (default): 1000 x 1000, rank 10, |Omega| = 6 r (2n - r) = 119,400 sampled entries,
+N(0,1) planted factors, tau = 5n, delta = 1.2/p, eps = 1e-4, float32 values / float64 Lanczos
+basis and projected SVD (the single-solve configuration of the paper's Table 1, first row).
+
+A step runs the whole path through the C-ABI: svt_create (Omega storage: CSR, CSC, permutation),
+svt_solve (kick with ||P_Omega M||_2, then Algorithm 1 until the relative residual on Omega is
+<= 1e-4) and svt_destroy.  `value` is SVT iterations per second over the timed steps (inputs
+resident in HBM); `e2e` is the same metric with the inputs copied from pinned host memory and the
+factors of X copied back inside every step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own problem (seed = rank): weak scaling, no data-path
+collective; the timing is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from svt_inputs import CONFIGS, config_problem  # noqa: E402
+
+METRIC = "SVT iters/s to 1e-4 rel. residual (time-to-1e-4 per solve)"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0810_3286_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("csrc_sha") != _kernel_source_sha():
+        return None
+    entry = t.get("classes", {}).get(kernel_class)
+    return None if entry is None else float(entry)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.device_index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names[1:], parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        return world, rank, local, dist
+    return world, rank, local, None
+
+
+def _max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def cpu_baseline(config_name, seed, max_iters=1):
+    """The float64 oracle as it stands on the host cores, on a bounded sample of the workload:
+    the kick (||P_Omega M||_2 by a dense Jacobi SVD) and the first `max_iters` SVT iterations."""
+    from oracle import svt as osvt
+    p = config_problem(config_name, seed)
+    t0 = time.perf_counter()
+    res = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), eps=1e-4,
+                   max_iters=max_iters, keep_trace=False)
+    dt = time.perf_counter() - t0
+    return {"value": res.iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": "kick + first %d SVT iteration(s) of the %dx%d rank-%d solve (float64, dense one-sided "
+                      "Jacobi SVD per iteration), %.1f s" % (res.iters, p.n1, p.n2, p.r, dt),
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, local, dist = _dist()
+    if rank != 0:
+        return 0
+    c = CONFIGS[args.config]
+    vals = []
+    base = None
+    for _ in range(args.warmup if args.warmup < 1 else 0):
+        pass
+    for k in range(max(1, args.steps)):
+        b = cpu_baseline(args.config, 0, max_iters=1)
+        vals.append(b["value"])
+        base = b
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * base["seconds"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: %dx%d rank %d, |Omega|=%d" % (args.config, c["n1"], c["n2"], c["r"],
+                                                                        config_problem(args.config, 0).nnz),
+                       "sample": base["sample"]},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": base["sample"]},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, dist = _dist()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_0810_3286_gb300 import Solver, build
+    build.build()
+    from paper_0810_3286_gb300 import _abi
+    stream = torch.cuda.current_stream()
+
+    p = config_problem(args.config, seed=rank)
+    tau, delta = p.tau_default(), p.delta_default()
+    rows_d = torch.from_numpy(p.rows).to(device)
+    cols_d = torch.from_numpy(p.cols).to(device)
+    vals_d = torch.from_numpy(p.vals).to(device)
+    rows_h = torch.from_numpy(p.rows).pin_memory()
+    cols_h = torch.from_numpy(p.cols).pin_memory()
+    vals_h = torch.from_numpy(p.vals).pin_memory()
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > 129 MB L2
+
+    def step_device(profile_classes=()):
+        s = Solver(p.n1, p.n2, rows_d, cols_d, vals_d, precision=args.precision, stream=stream)
+        if profile_classes:
+            s.set_profile(profile_classes)
+        res = s.solve(tau, delta, 1e-4, 27)
+        prof = s.profile() if profile_classes else None
+        launches = s.kernel_launches()
+        step_device.counters = s.counters()
+        s.close()
+        return res, launches, prof
+
+    U_h = torch.empty((p.n1, 27), dtype=torch.float64).pin_memory()
+    d_h = torch.empty(27, dtype=torch.float64).pin_memory()
+    V_h = torch.empty((p.n2, 27), dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        s = Solver(p.n1, p.n2, rows_h.numpy(), cols_h.numpy(), vals_h.numpy(), precision=args.precision,
+                   stream=stream)
+        res = s.solve(tau, delta, 1e-4, 27)
+        r = res["rank"]
+        st = s._L.svt_get_factors(s._ctx, U_h.data_ptr(), d_h.data_ptr(), V_h.data_ptr(), 27)
+        assert st == 0
+        launches = s.kernel_launches()
+        s.close()
+        return res, launches, r
+
+    # --- warm-up (also compiles nothing: the library is prebuilt) ---
+    for _ in range(args.warmup):
+        step_device()
+    # --- per-class profile of one untimed solve: which kernel class dominates the device time ---
+    _, _, prof_all = step_device(tuple(_abi.PROF_CLASSES))
+    counters = dict(step_device.counters)
+    shares = {k: v[1] for k, v in prof_all.items()}
+    tot = sum(shares.values()) or 1.0
+    hbm_classes = ["spmm", "spmm_t", "sddmm_update", "gram", "block_update", "combine"]
+    dominant = max(hbm_classes, key=lambda k: shares[k])
+    dominant_all = max(shares, key=lambda k: shares[k])
+
+    # --- timed region: K device-resident steps ---
+    clocks = ClockSampler(torch.cuda.current_device())
+    _barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    iters = 0
+    launches = 0
+    prof_timed = {}
+    results = []
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        l2_flush.zero_()
+        ev[k][0].record(stream)
+        res, nl, prof = step_device((dominant,))
+        ev[k][1].record(stream)
+        iters += res["iterations"]
+        launches += nl
+        results.append(res)
+        for c, (n, ms, by) in prof.items():
+            a = prof_timed.setdefault(c, [0, 0.0, 0.0])
+            a[0] += n; a[1] += ms; a[2] += by
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    _barrier(dist)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    total_s_max = _max_over_ranks(dist, total_s, device)
+    iters_all = _sum_over_ranks(dist, float(iters), device)
+    value = iters_all / total_s_max
+
+    # --- end to end through the C-ABI with host buffers ---
+    for _ in range(max(1, args.warmup // 2)):
+        step_e2e()
+    _barrier(dist)
+    torch.cuda.synchronize()
+    e2e_iters, e2e_r = 0, 0
+    t0 = time.perf_counter()
+    e2e_ev = []
+    for k in range(args.steps):
+        l2_flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, _, r = step_e2e()
+        b.record(stream)
+        e2e_ev.append((a, b))
+        e2e_iters += res["iterations"]
+        e2e_r = r
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
+    e2e_s = _max_over_ranks(dist, e2e_s, device)
+    e2e_iters = _sum_over_ranks(dist, float(e2e_iters), device)
+    _barrier(dist)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    n_l, ms_l, by_l = prof_timed.get(dominant, [0, 0.0, 0.0])
+    achieved = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
+    traffic = _traffic_for(dominant)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_kind": "%s copy bandwidth" % peak_kind,
+                "traffic": traffic, "launches_timed": n_l,
+                "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
+                "algorithmic_bytes_per_launch": by_l / n_l if n_l else None}
+    cpu = cpu_baseline(args.config, 0, max_iters=1) if not args.no_cpu_baseline else None
+    if cpu is not None:
+        cpu.pop("seconds", None)
+    c = CONFIGS[args.config]
+    mean_iters = float(np.mean([r["iterations"] for r in results]))
+    line = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * total_s_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "%s: %dx%d rank %d, |Omega|=%d (6 r(2n-r)), tau=5n, delta=1.2/p, eps=1e-4"
+                               % (args.config, c["n1"], c["n2"], c["r"], p.nnz),
+                   "precision": "%s values and sparse products, float64 Lanczos basis and projected SVD"
+                                % ("float32" if args.precision == "fp32" else "float64"),
+                   "step": "svt_create (Omega storage) + svt_solve (kick + iterations to 1e-4) + svt_destroy",
+                   "l2": "256 MB buffer written between steps (flush)", "parallelism": "replicas%d" % world},
+        "time_to_1e-4_ms": 1000.0 * total_s_max / args.steps,
+        "iterations_per_solve": mean_iters, "k0": results[0]["k0"], "rank": results[0]["rank"],
+        "final_residual": results[-1]["residual"], "wall_s": t_wall,
+        "clocks": clk,
+        "e2e": {"value": e2e_iters / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": int(p.nnz * (4 + 4 + 8)),
+                "d2h_bytes_per_step": int(8 * (p.n1 + p.n2 + 1) * e2e_r)},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernel_time_shares": {k: round(v / tot, 4) for k, v in shares.items()},
+        "dominant_kernel_class": dominant_all,
+        "solver_counters_per_solve": counters,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="single_1000", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -131,7 +131,7 @@ const char* svt_last_error(const svt_ctx* ctx);
  *   tau       threshold; <= 0 selects 5 sqrt(m n) (Sec. 5.2.1: tau = 5n for square matrices)
  *   delta     step size; <= 0 selects 1.2 m n / nnz (eq. (5.1))
  *   eps       tolerance of the stopping rule eq. (5.5); <= 0 selects 1e-4
- *   max_rank  capacity for the rank of X^k (1 .. 64); exceeding it returns SVT_ERR_RANK_LIMIT
+ *   max_rank  capacity for the rank of X^k (1 .. 27); exceeding it returns SVT_ERR_RANK_LIMIT
  *   k0        >= 0 uses this kick count instead of eq. (5.3); -1 = eq. (5.3)
  * Errors: SVT_ERR_ARG, SVT_ERR_NUMERIC, SVT_ERR_CUDA.
  */
@@ -199,6 +199,8 @@ svt_status svt_shrink(svt_ctx* ctx, double tau, int* r, double* sigma);
  *   svt_apply_Yt  Z (n x b, float64) = Y^T U for U (m x b, float64)  -- Y transpose times a block
  * Y is the current dual iterate; the arithmetic is that of the context's precision.  These are
  * the two products the Lanczos bidiagonalisation needs (Sec. 2.2 and Sec. 5.1.1).
+ * Asynchronous: the kernel is queued on the context stream and the call returns; V/U and W/Z must
+ * stay valid until the stream reaches it.  Pointers must be 16-byte aligned and b even.
  */
 svt_status svt_apply_Y(svt_ctx* ctx, const double* V, int b, double* W);
 svt_status svt_apply_Yt(svt_ctx* ctx, const double* U, int b, double* Z);
@@ -235,6 +237,31 @@ svt_status svt_load_state(svt_ctx* ctx, const void* buf, size_t bytes);
 
 /* Device kernels launched by this library so far on ctx (for launch accounting). */
 int64_t svt_kernel_launches(const svt_ctx* ctx);
+
+/*
+ * Kernel-class profile.  Classes (bit i of the mask = class i):
+ *   SVT_PROF_SPMM (Y V), SVT_PROF_SPMM_T (Y^T U), SVT_PROF_GRAM (basis Gram products),
+ *   SVT_PROF_BLOCK_UPDATE (P <- (P - Q C) R^-1), SVT_PROF_SMALL (b x b Cholesky steps),
+ *   SVT_PROF_JACOBI (projected SVD), SVT_PROF_COMBINE (Ritz vectors), SVT_PROF_SDDMM (fused X on
+ *   Omega + dual step).
+ * svt_set_profile selects the classes whose launches are bracketed by CUDA events on the context
+ * stream (0 = none) and clears the totals.  svt_get_profile writes, per class, the number of
+ * bracketed launch groups, their total device time in milliseconds and the algorithmic bytes they
+ * move (arrays of SVT_PROF_CLASSES entries; any pointer may be NULL).  Both synchronise the stream.
+ */
+enum { SVT_PROF_SPMM = 0, SVT_PROF_SPMM_T, SVT_PROF_GRAM, SVT_PROF_BLOCK_UPDATE, SVT_PROF_SMALL, SVT_PROF_JACOBI,
+       SVT_PROF_COMBINE, SVT_PROF_SDDMM, SVT_PROF_CLASSES };
+svt_status svt_set_profile(svt_ctx* ctx, unsigned int class_mask);
+svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+
+/*
+ * Cumulative solver counters since svt_create, written to out[0 .. min(n, 8)):
+ *   [0] Lanczos cycles, [1] sparse products, [2] projected-SVD calls, [3] Jacobi sweeps in them,
+ *   [4] basis columns deflated as numerically dependent, [5] largest orthonormality defect
+ *   max |P^T P - I| seen after the Cholesky pass, [6] kernel launches, [7] reserved (0).
+ * Synchronises the stream.
+ */
+svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);
 
 #ifdef __cplusplus
 }

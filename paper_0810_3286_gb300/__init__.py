@@ -216,6 +216,29 @@ class Solver:
     def kernel_launches(self) -> int:
         return int(self._L.svt_kernel_launches(self._ctx))
 
+    def counters(self):
+        """Cumulative solver counters (see svt_get_counters)."""
+        out = np.zeros(8)
+        _check(self._L.svt_get_counters(self._ctx, out.ctypes.data, 8), "svt_get_counters", self._ctx)
+        return dict(zip(_abi.COUNTER_NAMES, out.tolist()))
+
+    def set_profile(self, classes=()):
+        """Bracket the launches of the named kernel classes with CUDA events (see PROF_CLASSES)."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << _abi.PROF_CLASSES.index(c)
+        _check(self._L.svt_set_profile(self._ctx, mask), "svt_set_profile", self._ctx)
+
+    def profile(self):
+        """{class: (launch groups, total ms, algorithmic bytes)} since the last set_profile."""
+        n = len(_abi.PROF_CLASSES)
+        launches = np.zeros(n, np.int64)
+        ms = np.zeros(n)
+        by = np.zeros(n)
+        _check(self._L.svt_get_profile(self._ctx, launches.ctypes.data, ms.ctypes.data, by.ctypes.data),
+               "svt_get_profile", self._ctx)
+        return {c: (int(launches[i]), float(ms[i]), float(by[i])) for i, c in enumerate(_abi.PROF_CLASSES)}
+
 
 def sample_omega(m: int, n: int, nnz: int, seed: int, rows_out, cols_out, stream=None) -> None:
     """Device random-keys sampler of Omega into int32 device tensors rows_out/cols_out."""

@@ -109,7 +109,16 @@ PROTOTYPES = {
     "svt_save_state": (ctypes.c_int, [_ctxp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
     "svt_load_state": (ctypes.c_int, [_ctxp, _vp, ctypes.c_size_t]),
     "svt_kernel_launches": (ctypes.c_int64, [_ctxp]),
+    "svt_set_profile": (ctypes.c_int, [_ctxp, ctypes.c_uint]),
+    "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp]),
+    "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
 }
+
+COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "deflated_columns",
+                 "max_orth_defect", "kernel_launches", "reserved"]
+
+# kernel classes of svt_set_profile / svt_get_profile
+PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update"]
 
 _lock = threading.Lock()
 _lib = None

@@ -91,12 +91,25 @@ struct svt_ctx {
   // Lanczos workspace
   double *Ub = nullptr, *Vb = nullptr;   // block bases (blocks of rows x b)
   double *T = nullptr, *S = nullptr, *theta = nullptr, *Xl = nullptr, *Wr = nullptr, *res = nullptr;
-  double *G = nullptr, *gpart = nullptr, *coef = nullptr, *coef2 = nullptr, *colnorm0 = nullptr;
-  double *Rinv = nullptr, *Rkeep = nullptr, *scale = nullptr, *apply_tmp = nullptr;
+  double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
+  double *Rkeep = nullptr, *scale = nullptr;
+  bool two_corrections = false;           // set once an orthonormality defect above 1e-7 was seen
+  double* R2 = nullptr;                   // b x b product of the first correction and R1
+  unsigned long long* dcount = nullptr;   // device counters: [0] Jacobi calls [1] Jacobi sweeps
+                                          // [2] deflated columns [3] max orthonormality defect (bits)
   double *upd_partial = nullptr, *dscal = nullptr;
   unsigned int* err = nullptr;
   double* h_pin = nullptr;          // pinned host staging (theta, res, scalars)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // per-kernel-class profile (CUDA events around launches of the classes in prof_mask)
+  unsigned int prof_mask = 0;
+  std::vector<cudaEvent_t> prof_pool;
+  struct ProfRec { int cls; double bytes; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  double prof_ms[SVT_PROF_CLASSES] = {0};
+  double prof_bytes[SVT_PROF_CLASSES] = {0};
+  int64_t prof_n[SVT_PROF_CLASSES] = {0};
 
   // statistics of the last shrink
   int last_cycles = 0, last_spmm = 0, last_s = 0, last_passes = 0;
@@ -163,8 +176,52 @@ static svt_status launched(svt_ctx* c, int n) {
   return SVT_OK;
 }
 
+static cudaEvent_t prof_event(svt_ctx* c) {
+  if (!c->prof_pool.empty()) {
+    cudaEvent_t e = c->prof_pool.back();
+    c->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { (void)cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Runs `f` (which issues the launches of one kernel class and returns their count); when the
+// class is selected by the profile mask, brackets the launches with CUDA events on the context
+// stream and records the algorithmic bytes they move.
+template <class F>
+static int prof_launch(svt_ctx* c, int cls, double bytes, F&& f) {
+  if (!(c->prof_mask & (1u << cls))) return f();
+  cudaEvent_t a = prof_event(c), b = prof_event(c);
+  if (!a || !b) return f();
+  cudaEventRecord(a, c->st);
+  int n = f();
+  cudaEventRecord(b, c->st);
+  c->prof_pending.push_back({cls, bytes, a, b});
+  return n;
+}
+
+// Called after the stream has drained: folds the recorded event pairs into the totals.
+static void prof_harvest(svt_ctx* c) {
+  for (auto& r : c->prof_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.cls] += ms;
+      c->prof_bytes[r.cls] += r.bytes;
+      c->prof_n[r.cls] += 1;
+    } else {
+      (void)cudaGetLastError();
+    }
+    c->prof_pool.push_back(r.a);
+    c->prof_pool.push_back(r.b);
+  }
+  c->prof_pending.clear();
+}
+
 static svt_status sync_and_check(svt_ctx* c) {
   CU(c, cudaStreamSynchronize(c->st));
+  prof_harvest(c);
   unsigned int e = 0;
   CU(c, cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
   if (e) {
@@ -197,6 +254,18 @@ static uint64_t next_seed(svt_ctx* c) {
 static void* ycur_csr(svt_ctx* c) { return c->Ycsr[c->ycur]; }
 static void* ycur_csc(svt_ctx* c) { return c->Ycsc[c->ycur]; }
 
+// Algorithmic bytes of one sparse product Out (n_out x b) = S X (X: n_in x b, float64 blocks):
+// index + value stream, segment pointers, each row of X read once, Out written once.
+static double spmm_bytes(const svt_ctx* c, int n_out, int n_in, int b) {
+  return (double)c->nnz * (4.0 + (double)c->vbytes) + 4.0 * (n_out + 1) + 8.0 * b * ((double)n_in + n_out);
+}
+
+// Algorithmic bytes of the fused X-on-Omega + dual step: col_idx, csr_to_csc, M, Y read, Y and its
+// column-major copy written, row pointers, the factors read once.
+static double sddmm_bytes(const svt_ctx* c, int r) {
+  return (double)c->nnz * (8.0 + 4.0 * (double)c->vbytes) + 4.0 * (c->m + 1) + 8.0 * r * ((double)c->m + c->n);
+}
+
 // ------------------------------------------------------------------------------------------------
 // Block CGS2 + Cholesky QR of P (rows x b) against nq orthonormal blocks Q (stride q_stride).
 // Coefficients: P_in = Q (C1 + C2) + P_out (R2 R1); written to Tcol / Tdiag when given.
@@ -204,20 +273,43 @@ static void* ycur_csc(svt_ctx* c) { return c->Ycsc[c->ycur]; }
 static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long long q_stride, int nq, int rows, int b,
                                  double* Tcol, double* Tdiag) {
   int l = 0;
+  const double gram_q = 8.0 * rows * (nq + 1) * b, gram_p = 8.0 * rows * b;
+  const double upd_q = 8.0 * rows * (nq + 2) * b, upd_p = 16.0 * rows * b;
+  const double* G1 = nullptr;
   if (nq > 0) {
-    l += launch_gram(Q, q_stride, nq, P, rows, b, c->gpart, c->G, c->st);
-    l += launch_orth_small(0, c->G, nq, b, c->coef, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, nullptr, kKMax,
-                           nullptr, c->err, c->st);
-    l += launch_block_update(Q, q_stride, nq, c->coef, nullptr, P, rows, b, c->st);
+    // C1 = Q^T P; then P <- P - Q C1 fused with the Gram [Q, P]^T P of the projected block
+    l += prof_launch(c, SVT_PROF_GRAM, gram_q,
+                     [&] { return launch_gram(Q, q_stride, nq, P, rows, b, c->gpart, c->G1, c->st); });
+    l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_q + gram_q, [&] {
+      return launch_update_gram(0, Q, q_stride, nq, c->G1, nullptr, nullptr, P, rows, b, c->gpart, c->G2, c->st,
+                                c->G1, Tcol, kKMax);
+    });
+    G1 = c->G1;
+  } else {
+    l += prof_launch(c, SVT_PROF_GRAM, gram_p,
+                     [&] { return launch_gram(nullptr, 0, 0, P, rows, b, c->gpart, c->G2, c->st); });
   }
-  l += launch_gram(Q, q_stride, nq, P, rows, b, c->gpart, c->G, c->st);
-  l += launch_orth_small(1, c->G, nq, b, c->coef, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, nullptr, kKMax, nullptr,
-                         c->err, c->st);
-  l += launch_block_update(Q, q_stride, nq, c->coef2, c->Rinv, P, rows, b, c->st);
-  l += launch_gram(nullptr, 0, 0, P, rows, b, c->gpart, c->G, c->st);
-  l += launch_orth_small(2, c->G, nq, b, nq > 0 ? c->coef : nullptr, c->coef2, c->colnorm0, c->Rinv, c->Rkeep, Tcol,
-                         kKMax, Tdiag, c->err, c->st);
-  l += launch_block_update(nullptr, 0, 0, nullptr, c->Rinv, P, rows, b, c->st);
+  l += prof_launch(c, SVT_PROF_SMALL, 0.0,
+                   [&] { return launch_chol(G1, c->G2, nq, b, c->R1, c->dinv, c->dcount, c->st); });
+  // P <- (P - Q C2) R1^-1 fused with the Gram P^T P
+  l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_q + gram_p, [&] {
+    return launch_update_gram(1, Q, q_stride, nq, c->G2, c->R1, c->dinv, P, rows, b, c->gpart, c->G3, c->st);
+  });
+  if (!c->two_corrections) {
+    l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_p, [&] {
+      return launch_correct(c->G3, c->R1, Tdiag, kKMax, nullptr, P, rows, b, c->dcount, c->st);
+    });
+  } else {
+    // ill-conditioned blocks seen: a second first-order correction (orthonormality O(|E|^4))
+    l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_p, [&] {
+      return launch_correct(c->G3, c->R1, nullptr, kKMax, c->R2, P, rows, b, c->dcount, c->st);
+    });
+    l += prof_launch(c, SVT_PROF_GRAM, gram_p,
+                     [&] { return launch_gram(nullptr, 0, 0, P, rows, b, c->gpart, c->G3, c->st); });
+    l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_p, [&] {
+      return launch_correct(c->G3, c->R2, Tdiag, kKMax, nullptr, P, rows, b, nullptr, c->st);
+    });
+  }
   return launched(c, l);
 }
 
@@ -233,11 +325,13 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
   for (int j = 0; j < J; ++j) {
     double* Uj = c->Ub + j * su;
     double* Vj = c->Vb + j * sv;
-    l += launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, Uj, m, b, c->st);
+    l += prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b),
+                     [&] { return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, Uj, m, b, c->st, c->nnz); });
     TRY(launched(c, l)); l = 0;
     TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b));
     double* Vn = c->Vb + (j + 1) * sv;
-    l += launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, Vn, n, b, c->st);
+    l += prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b),
+                     [&] { return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, Vn, n, b, c->st, c->nnz); });
     TRY(launched(c, l)); l = 0;
     TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr));
   }
@@ -245,8 +339,16 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
   // leading dimension b, so compact it first.
   CU(c, cudaMemcpy2DAsync(c->Rkeep, b * sizeof(double), c->S, kKMax * sizeof(double), b * sizeof(double), b,
                           cudaMemcpyDeviceToDevice, c->st));
-  const double tol_j = 1e-15;
-  l += launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err, c->st);
+  // one-sided Jacobi stops when every column pair is orthogonal to the rounding level of a length-K
+  // dot product
+  const double tol_j = std::max(1e-15, 2.0 * K * 1.1102230246251565e-16);
+  l += prof_launch(c, SVT_PROF_JACOBI, 24.0 * K * K, [&] {
+    if (c->prec == SVT_FP64)
+      return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
+                              c->dcount, c->st);
+    return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, b, 2e-6, 60, c->err,
+                                  c->dcount, c->st);
+  });
   TRY(launched(c, l));
   c->last_spmm += 2 * J;
   c->total_spmm += 2 * J;
@@ -254,7 +356,13 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
   c->total_cycles += 1;
   CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax + 1, c->dcount + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   TRY(sync_and_check(c));
+  {
+    double defect = 0.0;
+    std::memcpy(&defect, c->h_pin + 3 * kKMax + 1, sizeof defect);
+    if (defect > 1e-7) c->two_corrections = true;
+  }
   *theta_h = c->h_pin;
   *res_h = c->h_pin + kKMax;
   return SVT_OK;
@@ -279,7 +387,9 @@ static svt_status keep_ritz(svt_ctx* c, int b, int J, int cols) {
   const int n = (int)c->n;
   const int K = J * b;
   cols = std::min(cols, std::min(K, kBMax));
-  int l = launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, cols, nullptr, c->Vwarm, c->st);
+  int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * n * (K + cols), [&] {
+    return launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, cols, nullptr, c->Vwarm, c->st);
+  });
   c->warm_cols = cols;
   return launched(c, l);
 }
@@ -288,8 +398,10 @@ static svt_status keep_ritz(svt_ctx* c, int b, int J, int cols) {
 // until the rank policy stops: s = s_init; converge the first s triplets; while sigma_s > tau,
 // s += ell (reusing the converged Ritz vectors as the start block).  On return theta_out holds the
 // converged values (host), *s_out the final s, *K_out/J_out/b_out the last cycle's shape.
+// strict: the first s_init triplets must all meet the residual tolerance and s never grows (used
+// for ||P_Omega M||_2, where the value itself matters).
 static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<double>& theta_out, int* s_out,
-                              int* passes_out, int* b_out, int* J_out) {
+                              int* passes_out, int* b_out, int* J_out, bool strict = false) {
   const int kmin = (int)std::min(c->m, c->n);
   const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-10 : 1e-6);
   int s = std::min(s_init, kmin);
@@ -306,12 +418,22 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     TRY(lanczos_cycle(c, b, J, &th, &rs));
     const int K = J * b;
     const int s_eff = std::min(s, K);
+    // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
+    // theta_s > tau already proves sigma_s > tau: the rank policy grows s without waiting for
+    // convergence.  Otherwise every Ritz triplet above tau must be converged to `tol`, and the
+    // first Ritz value at or below tau must be bounded away from it (theta + residual <= tau).
+    const bool grow = !strict && th[s_eff - 1] > tau && s < kmin;
     int conv = 0;
-    while (conv < s_eff && rs[conv] <= tol * th[0]) ++conv;
-    const bool all_conv = conv >= s_eff;
-    if (all_conv) {
-      const double last = th[s_eff - 1];
-      if (last > tau && s < kmin) {
+    bool all_conv = !grow;
+    for (int i = 0; i < s_eff && all_conv; ++i) {
+      const bool above = strict || th[i] > tau;
+      const bool ok = rs[i] <= tol * th[0] || (!above && th[i] + rs[i] <= tau);
+      if (!ok) all_conv = false;
+      else ++conv;
+      if (!above) break;
+    }
+    if (all_conv || grow) {
+      if (grow) {
         if (s + c->opt.ell > kMaxRankCap + 1) {
           theta_out.assign(th, th + s_eff);
           *s_out = s;
@@ -335,7 +457,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     }
     if (cyc + 1 >= max_cycles)
       return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
-                  max_cycles, conv, s_eff, rs[conv] / th[0]);
+                  max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
     TRY(keep_ritz(c, b, J, b));
     TRY(set_start_block(c, b, b));
   }
@@ -360,9 +482,11 @@ static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out)
   if (r > 0) {
     std::memcpy(c->h_pin + 2 * kKMax, c->d_host.data(), sizeof(double) * r);
     CU(c, cudaMemcpyAsync(c->scale, c->h_pin + 2 * kKMax, sizeof(double) * r, cudaMemcpyHostToDevice, c->st));
-    l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, nullptr, c->Uf, c->st);
-    l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, c->scale, c->Ut, c->st);
-    l += launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, r, nullptr, c->Vf, c->st);
+    l += prof_launch(c, SVT_PROF_COMBINE, 8.0 * (2.0 * m * (K + r) + n * (K + r)), [&] {
+      return launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, nullptr, c->Uf, c->st) +
+             launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, c->scale, c->Ut, c->st) +
+             launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, r, nullptr, c->Vf, c->st);
+    });
   }
   TRY(launched(c, l));
   // warm start of the next shrink: the leading right Ritz vectors
@@ -401,6 +525,11 @@ extern "C" void svt_destroy(svt_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
+  for (auto& r : c->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   delete c;
@@ -552,13 +681,19 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   A(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
   A(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
   A(dalloc_t(c, &c->res, kKMax));
-  A(dalloc_t(c, &c->G, 128 * 32));
+  A(dalloc_t(c, &c->G1, 128 * 32));
+  A(dalloc_t(c, &c->G2, 128 * 32));
+  A(dalloc_t(c, &c->G3, 128 * 32));
+  A(dalloc_t(c, &c->R1, kBMax * kBMax));
+  A(dalloc_t(c, &c->R2, kBMax * kBMax));
+  A(dalloc_t(c, &c->dinv, kBMax));
+  A(dalloc_t(c, &c->dcount, 8));
+  if (cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->st) != cudaSuccess) {
+    fail(c, SVT_ERR_CUDA, "memset");
+    return bail(SVT_ERR_CUDA);
+  }
   // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
   A(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
-  A(dalloc_t(c, &c->coef, (size_t)kKMax * kBMax));
-  A(dalloc_t(c, &c->coef2, (size_t)kKMax * kBMax));
-  A(dalloc_t(c, &c->colnorm0, kBMax));
-  A(dalloc_t(c, &c->Rinv, kBMax * kBMax));
   A(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
   A(dalloc_t(c, &c->scale, 64));
   A(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
@@ -623,7 +758,7 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
   std::vector<double> th;
   int s = 0, passes = 0, b = 0, J = 0;
   // huge tau so that the rank policy stops after the first converged triplet
-  TRY(partial_svd(c, 1, INFINITY, th, &s, &passes, &b, &J));
+  TRY(partial_svd(c, 1, INFINITY, th, &s, &passes, &b, &J, /*strict=*/true));
   c->norm2 = th.empty() ? 0.0 : th[0];
   if (!(c->norm2 > 0.0)) return fail(c, SVT_ERR_NUMERIC, "||P_Omega M||_2 is zero");
   TRY(keep_ritz(c, b, J, std::min(b, 8)));
@@ -645,9 +780,11 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   int r = 0;
   TRY(shrink_current(c, c->tau, c->r + 1, &r));
   const int nxt = 1 - c->ycur;
-  TRY(launched(c, launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
-                                      c->Ycsc[nxt], c->Ut, c->Vf, r, (int)c->m, c->delta, c->upd_partial, c->dscal,
-                                      c->err, c->st)));
+  TRY(launched(c, prof_launch(c, SVT_PROF_SDDMM, sddmm_bytes(c, r), [&] {
+    return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
+                               c->Ycsc[nxt], c->Ut, c->Vf, r, (int)c->m, c->delta, c->upd_partial, c->dscal, c->err,
+                               c->st);
+  })));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaEventRecord(c->ev1, c->st));
   TRY(sync_and_check(c));
@@ -790,16 +927,18 @@ extern "C" svt_status svt_apply_Y(svt_ctx* c, const double* V, int b, double* W)
   if (!c || !V || !W) return SVT_ERR_ARG;
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(V) || !aligned16(W)) return fail(c, SVT_ERR_ARG, "V and W must be 16-byte aligned");
-  TRY(launched(c, launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), V, W, (int)c->m, b, c->st)));
-  return sync_and_check(c);
+  return launched(c, prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, (int)c->m, (int)c->n, b), [&] {
+    return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), V, W, (int)c->m, b, c->st, c->nnz);
+  }));
 }
 
 extern "C" svt_status svt_apply_Yt(svt_ctx* c, const double* U, int b, double* Z) {
   if (!c || !U || !Z) return SVT_ERR_ARG;
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(U) || !aligned16(Z)) return fail(c, SVT_ERR_ARG, "U and Z must be 16-byte aligned");
-  TRY(launched(c, launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), U, Z, (int)c->n, b, c->st)));
-  return sync_and_check(c);
+  return launched(c, prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, (int)c->n, (int)c->m, b), [&] {
+    return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), U, Z, (int)c->n, b, c->st, c->nnz);
+  }));
 }
 
 extern "C" svt_status svt_sddmm_update(svt_ctx* c, const double* Ut, const double* V, int r, double delta,
@@ -909,7 +1048,7 @@ struct StateHeader {
   int32_t prec, r, warm_cols, configured;
   int64_t k0, k;
   double tau, delta, eps, norm2;
-  int32_t max_rank, ycur_unused;
+  int32_t max_rank, flags;   // flags bit 0: two orthonormality corrections
   uint64_t rng_counter;
 };
 
@@ -927,6 +1066,7 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   h.magic = kStateMagic; h.m = c->m; h.n = c->n; h.nnz = c->nnz; h.prec = c->prec; h.r = c->r;
   h.warm_cols = c->warm_cols; h.configured = c->configured; h.k0 = c->k0; h.k = c->k; h.tau = c->tau;
   h.delta = c->delta; h.eps = c->eps; h.norm2 = c->norm2; h.max_rank = c->max_rank; h.rng_counter = c->rng_counter;
+  h.flags = c->two_corrections ? 1 : 0;
   char* p = (char*)buf;
   std::memcpy(p, &h, sizeof h); p += sizeof h;
   CU(c, cudaMemcpyAsync(p, ycur_csr(c), c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st)); p += c->nnz * c->vbytes;
@@ -952,6 +1092,7 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
   c->r = h.r; c->warm_cols = h.warm_cols; c->configured = h.configured != 0; c->k0 = h.k0; c->k = h.k;
   c->tau = h.tau; c->delta = h.delta; c->eps = h.eps; c->norm2 = h.norm2; c->max_rank = h.max_rank;
   c->rng_counter = h.rng_counter;
+  c->two_corrections = (h.flags & 1) != 0;
   if (bytes < state_bytes(c)) return fail(c, SVT_ERR_ARG, "state buffer too small");
   const char* p = (const char*)buf + sizeof h;
   CU(c, cudaMemcpyAsync(ycur_csr(c), p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st)); p += c->nnz * c->vbytes;
@@ -973,4 +1114,45 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
     cudaFree(tmp);
   }
   return sync_and_check(c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Profile
+// ------------------------------------------------------------------------------------------------
+extern "C" svt_status svt_set_profile(svt_ctx* c, unsigned int class_mask) {
+  if (!c) return SVT_ERR_ARG;
+  CU(c, cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  c->prof_mask = class_mask;
+  for (int i = 0; i < SVT_PROF_CLASSES; ++i) {
+    c->prof_ms[i] = 0.0;
+    c->prof_bytes[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms, double* bytes) {
+  if (!c) return SVT_ERR_ARG;
+  CU(c, cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  for (int i = 0; i < SVT_PROF_CLASSES; ++i) {
+    if (launches) launches[i] = c->prof_n[i];
+    if (ms) ms[i] = c->prof_ms[i];
+    if (bytes) bytes[i] = c->prof_bytes[i];
+  }
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_get_counters(svt_ctx* c, double* out, int n) {
+  if (!c || !out || n < 0) return SVT_ERR_ARG;
+  unsigned long long dc[8] = {0};
+  CU(c, cudaStreamSynchronize(c->st));
+  CU(c, cudaMemcpy(dc, c->dcount, sizeof dc, cudaMemcpyDeviceToHost));
+  double maxdef = 0.0;
+  std::memcpy(&maxdef, &dc[3], sizeof maxdef);
+  const double v[8] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],
+                       maxdef, (double)c->launches, 0.0};
+  for (int i = 0; i < n && i < 8; ++i) out[i] = v[i];
+  return SVT_OK;
 }

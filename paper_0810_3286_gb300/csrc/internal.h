@@ -55,35 +55,46 @@ int launch_omega_compact(uint64_t seed, long long N, long long n_cols, const voi
 // ----- per-iteration kernels -------------------------------------------------------------------
 // Out (n_out x b) = S X with S given in compressed segments (ptr, idx, val) and X (n_in x b).
 // precision 0: float64 values and accumulation; 1: float32 values and accumulation.
+// nnz (the total segment length) chooses how many warps share a segment.
 int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
-                double* Out, int n_out, int b, cudaStream_t st);
+                double* Out, int n_out, int b, cudaStream_t st, long long nnz);
 
 // Gram of a tall block against a basis: G ((nq+1) b x b) = [Q_0 .. Q_{nq-1}, P]^T P, where the Q_i
 // are n x b blocks spaced `q_stride` doubles apart.  partial: gram_partial_doubles(...) doubles.
 long long gram_partial_doubles(int n, int nq, int b);
+// With Tcol given, the coefficient rows (the first nq b rows of G) are also written to Tcol
+// (leading dimension ldT) as Gprev + G (Gprev may be NULL).
 int launch_gram(const double* Q, long long q_stride, int nq, const double* P, int n, int b, double* partial,
-                double* G, cudaStream_t st);
+                double* G, cudaStream_t st, const double* Gprev = nullptr, double* Tcol = nullptr, int ldT = 0);
 
-// P <- (P - Q C) Rinv  (C: nq b x b; Rinv: b x b upper triangular, or NULL = identity)
-int launch_block_update(const double* Q, long long q_stride, int nq, const double* C, const double* Rinv,
-                        double* P, int n, int b, cudaStream_t st);
-
-// Small-matrix step of block CGS2 + Cholesky QR.  See lanczos_orth_step in kernels.cu.
-// mode 0: first pass.  In: G1 = [Q,P]^T P (before projection).  Writes C1 (coefficients,
-//         nq b x b) to coef, keeps ||p_c||^2 in colnorm0.
-// mode 1: after P -= Q C1.  In: G2 = [Q,P]^T P.  Writes C2 to coef2, R1 = chol(P^T P - C2^T C2)
-//         (deflating columns whose norm fell below sqrt(eps) of colnorm0) and Rinv1.
-// mode 2: after P <- (P - Q C2) Rinv1.  In: G3 = P^T P.  R2 = chol(G3), Rinv2, and the final
-//         coefficient block: Tcol[0..nq b) = C1 + C2, diag block R2 R1 into Tdiag.
-int launch_orth_small(int mode, const double* G, int nq, int b, double* coef, double* coef2, double* colnorm0,
-                      double* Rinv, double* Rkeep, double* Tcol, int ldT, double* Tdiag, unsigned int* err,
-                      cudaStream_t st);
+// Block orthonormalisation steps (orth.cu).  C is the leading K x b part of a Gram result (K = nq b).
+// Fused update + Gram (both kernels of a Gram: partial products and their fixed-order sum into G):
+//   mode 0: P <- P - Q C, then G = [Q, P]^T P;  mode 1: P <- (P - Q C) R^-1, then G = P^T P.
+int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, const double* C, const double* R,
+                       const double* dinv, double* P, int n, int b, double* partial, double* G, cudaStream_t st,
+                       const double* Gprev = nullptr, double* Tcol = nullptr, int ldT = 0);
+// R = chol(A) with deflation, A the trailing b x b block of G2; dinv = 1/diag(R) (0 if deflated);
+// G1 (may be NULL when nq == 0) gives the column norms before the projections.
+// counters[2] += deflated columns.
+int launch_chol(const double* G1, const double* G2, int nq, int b, double* R, double* dinv,
+                unsigned long long* counters, cudaStream_t st);
+// P <- P (I - U(G3 - I)); (I + U(G3 - I)) R1 -> Tdiag (ld ldT) and/or Rout (b x b);
+// counters[3] = max |G3 - I| (as float64 bits)
+int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, double* Rout, double* P, int n, int b,
+                   unsigned long long* counters, cudaStream_t st);
 
 // Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT): T = Xl diag(theta) Wr^T,
 // theta decreasing; Xl, Wr written K x K row-major.  Also res[i] = || S (Xl rows [K-b, K), column i) ||
 // for the b x b block S (upper triangular, may be NULL -> res = 0).
+// counters[0] += 1, counters[1] += sweeps.
 int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl, double* Wr,
-                     double* res, double tol, int max_sweeps, unsigned int* err, cudaStream_t st);
+                     double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
+                     cudaStream_t st);
+
+// Float32-rotation Jacobi with float64 Ritz values for the leading nvec triplets (see dense.cu).
+int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,
+                           double* Wr, double* res, int nvec, double tol, int max_sweeps, unsigned int* err,
+                           unsigned long long* counters, cudaStream_t st);
 
 // Out (n x s) = sum over blocks i of B_i (n x b) W[i b .. i b + b, 0 .. s) , columns scaled by
 // scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).

@@ -1,0 +1,426 @@
+// Projected SVD of the Lanczos partial SVD: T (K x K, K = J b <= 96) = Xl diag(theta) Wr^T by the
+// one-sided (Hestenes) Jacobi method, in one CTA.  Sec. 5.1.1: the singular values of the small
+// projected matrix are the Ritz values of Y, compared against tau by the rank policy.
+//
+// Layout: columns of G (= T, rotated in place) and of W (the accumulated rotations) live in shared
+// memory, column-major.  One warp per column pair: in each of the K-1 rounds of a sweep the K/2
+// disjoint pairs of a round-robin tournament are rotated in parallel; a warp holds its two columns
+// of G and W in registers (rows lane, lane+32, lane+64), reduces the three inner products with
+// butterfly shuffles, rotates and writes back; one barrier per round.
+//
+// Two arithmetic variants:
+//   * float64 path: rotations in float64.  GB300's float64 divide and square root take ~650
+//     cycles each, so the rotation parameters use float32 reciprocal / reciprocal-square-root
+//     seeds refined by Newton steps in float64 (two steps for the cosine, which keeps every
+//     rotation orthogonal to float64 rounding).
+//   * float32 path: rotations in float32 (the float64 rate is 1/64 of float32 on GB300); then, for
+//     the leading nvec right vectors w (renormalised in float64), theta = ||T w|| and
+//     x = T w / theta are formed in float64, so the values compared against tau are float64
+//     Rayleigh quotients, exact to second order in the float32 angle error of w.
+// Residual estimates of the Lanczos relation: res_k = || S x_k[last b rows] || with S the b x b
+// upper triangular factor of the last block (Y^T U_J = V T^T + V_{J+1} S E_J^T).
+#include "common.cuh"
+#include "internal.h"
+
+namespace svt {
+
+static constexpr int JMAXK = 96;
+static constexpr int JMAXB = 32;
+
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = y * (2.0 - x * y);
+  y = y * (2.0 - x * y);
+  return y;
+}
+__device__ __forceinline__ double rsqrt_nr(double x, int steps) {
+  double y = (double)rsqrtf((float)x);
+  for (int i = 0; i < steps; ++i) y = y * (1.5 - 0.5 * x * y * y);
+  return y;
+}
+
+template <typename R>
+struct Rot;
+
+template <>
+struct Rot<float> {
+  // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2)
+  static __device__ __forceinline__ void params(float al, float be, float ga, float& c, float& s) {
+    float zeta = __fdividef(be - al, 2.f * ga);
+    float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    c = rsqrtf(fmaf(t, t, 1.f));
+    s = c * t;
+  }
+};
+
+template <>
+struct Rot<double> {
+  static __device__ __forceinline__ void params(double al, double be, double ga, double& c, double& s) {
+    const double zeta = (be - al) * rcp_nr(2.0 * ga);
+    const double z2 = fma(zeta, zeta, 1.0);
+    const double h = z2 * rsqrt_nr(z2, 2);                 // sqrt(1 + zeta^2)
+    const double t = copysign(1.0, zeta) * rcp_nr(fabs(zeta) + h);
+    c = rsqrt_nr(fma(t, t, 1.0), 2);
+    s = c * t;
+  }
+};
+
+__device__ __forceinline__ float shfl_xor_r(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor_r(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+
+// Sweeps of the one-sided Jacobi method on G (K x K, column-major in shared memory), accumulating
+// the rotations in W.  JL lanes per column pair (JR = ceil(96 / JL) rows each), 32 / JL pairs per
+// warp: the rotation parameters of four pairs come out of one warp instruction, and the inner
+// products need only log2(JL) butterfly steps.  Returns the number of sweeps taken.
+static constexpr int JL = 8;
+
+template <typename R>
+__device__ __forceinline__ R shfl_grp(R v, int o) { return shfl_xor_r(v, o); }
+
+template <typename R, int JR>   // JR = rows per lane = ceil(K / JL), a compile-time bound
+__device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gl = lane & (JL - 1);                 // lane inside the pair group
+  const int gsub = lane / JL;                     // pair slot inside the warp
+  const int npairs = K / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int round = 0; round < K - 1; ++round) {
+      const unsigned char* rs = sched + 2 * round * npairs;
+      for (int base = warp * (32 / JL); base < npairs; base += nw * (32 / JL)) {   // warp-uniform
+        const int pr = base + gsub;
+        const bool has = pr < npairs;
+        const int p = has ? rs[2 * pr] : 0, q = has ? rs[2 * pr + 1] : 0;
+        R* gp = G + p * K;
+        R* gq = G + q * K;
+        R a[JR], bq[JR];
+        R al = 0, be = 0, ga = 0;
+#pragma unroll
+        for (int k = 0; k < JR; ++k) {
+          const int r = gl + JL * k;
+          const bool in = has && r < K;
+          a[k] = in ? gp[r] : R(0);
+          bq[k] = in ? gq[r] : R(0);
+          al += a[k] * a[k];
+          be += bq[k] * bq[k];
+          ga += a[k] * bq[k];
+        }
+#pragma unroll
+        for (int o = 1; o < JL; o <<= 1) {
+          al += shfl_grp(al, o);
+          be += shfl_grp(be, o);
+          ga += shfl_grp(ga, o);
+        }
+        if (has && ga != R(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          R c, s;
+          Rot<R>::params(al, be, ga, c, s);
+          R* wp = W + p * K;
+          R* wq = W + q * K;
+#pragma unroll
+          for (int k = 0; k < JR; ++k) {
+            const int r = gl + JL * k;
+            if (r < K) {
+              gp[r] = c * a[k] - s * bq[k];
+              gq[r] = s * a[k] + c * bq[k];
+              const R wa = wp[r], wb = wq[r];
+              wp[r] = c * wa - s * wb;
+              wq[r] = s * wa + c * wb;
+            }
+          }
+          if (gl == 0) *flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!*flag) break;
+    __syncthreads();
+  }
+  return sweep + 1;
+}
+
+// Round-robin tournament: in round r, pair 0 is (K-1, r) and pair i >= 1 is
+// ((r + i) mod (K-1), (r - i) mod (K-1)); every pair of columns meets once per sweep.
+__device__ void build_schedule(unsigned char* sched, int K) {
+  const int npairs = K / 2;
+  for (int e = threadIdx.x; e < (K - 1) * npairs; e += blockDim.x) {
+    const int round = e / npairs, i = e - round * npairs;
+    int p, q;
+    if (i == 0) { p = K - 1; q = round; }
+    else { p = (round + i) % (K - 1); q = (round - i + (K - 1)) % (K - 1); }
+    if (p > q) { int x = p; p = q; q = x; }
+    sched[2 * e] = (unsigned char)p;
+    sched[2 * e + 1] = (unsigned char)q;
+  }
+}
+
+// Rank of every column norm (decreasing, ties by index) -> order[rank] = column.
+template <typename R>
+__device__ void sort_columns(const R* nrm, int* order, int K) {
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    int rank = 0;
+    for (int c2 = 0; c2 < K; ++c2)
+      if (nrm[c2] > nrm[c] || (nrm[c2] == nrm[c] && c2 < c)) ++rank;
+    order[rank] = c;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// float64 path
+// ------------------------------------------------------------------------------------------------
+template <int JR>
+__global__ void __launch_bounds__(512)
+k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
+             double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
+             double tol, int max_sweeps, unsigned int* err, unsigned long long* counters) {
+  extern __shared__ double sm64[];
+  double* G = sm64;                   // K x K column-major
+  double* W = G + K * K;              // K x K column-major
+  double* nrm = W + K * K;            // K
+  double* rnrm = nrm + K;             // K: 1 / nrm (0 for a zero column)
+  int* order = (int*)(rnrm + K);      // K
+  unsigned char* sched = (unsigned char*)(order + K);
+  __shared__ int flag;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, c = e - i * K;
+    G[c * K + i] = T[i * ldT + c];
+    W[c * K + i] = (i == c) ? 1.0 : 0.0;
+  }
+  build_schedule(sched, K);
+  __syncthreads();
+  const int sweeps = jacobi_sweeps<double, JR>(G, W, sched, K, tol, max_sweeps, &flag);
+  if (threadIdx.x == 0) {
+    if (sweeps > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
+    if (counters) {
+      atomicAdd(&counters[0], 1ULL);
+      atomicAdd(&counters[1], (unsigned long long)sweeps);
+    }
+  }
+  // column norms (one warp per column)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < K; c += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
+      nrm[c] = th;
+      rnrm[c] = th > 0.0 ? rcp_nr(th) : 0.0;
+    }
+  }
+  __syncthreads();
+  sort_columns<double>(nrm, order, K);
+  __syncthreads();
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, k = e - i * K;
+    const int c = order[k];
+    Xl[i * K + k] = G[c * K + i] * rnrm[c];
+    Wr[i * K + k] = W[c * K + i];
+  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x) theta[k] = nrm[order[k]];
+  // residual estimates, one warp per triplet
+  for (int k = warp; k < K; k += nw) {
+    double r2 = 0.0;
+    if (S) {
+      const int c = order[k];
+      const double inv = rnrm[c];
+      for (int e = lane; e < b; e += 32) {
+        double v = 0.0;
+        for (int d = e; d < b; ++d) v += S[e * b + d] * G[c * K + (K - b + d)];
+        v *= inv;
+        r2 += v * v;
+      }
+      r2 = warp_sum(r2);
+    }
+    if (lane == 0) res[k] = sqrt(r2);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// float32 rotations + float64 Ritz values
+// ------------------------------------------------------------------------------------------------
+template <int JR>
+__global__ void __launch_bounds__(512)
+k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
+               double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
+               int nvec, float tol, int max_sweeps, unsigned int* err, unsigned long long* counters) {
+  extern __shared__ double smm[];
+  double* Td = smm;                         // K x K row-major, float64
+  double* wv = Td + K * K;                  // nvec x K normalised right vectors (float64)
+  double* gx = wv + nvec * K;               // nvec x K: T w
+  float* G = (float*)(gx + nvec * K);       // K x K column-major
+  float* W = G + K * K;                     // K x K column-major
+  float* nrm = W + K * K;                   // K
+  int* order = (int*)(nrm + K);             // K
+  unsigned char* sched = (unsigned char*)(order + K);
+  __shared__ int flag;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, c = e - i * K;
+    const double v = T[i * ldT + c];
+    Td[e] = v;
+    G[c * K + i] = (float)v;
+    W[c * K + i] = (i == c) ? 1.f : 0.f;
+  }
+  build_schedule(sched, K);
+  __syncthreads();
+  const int sweeps = jacobi_sweeps<float, JR>(G, W, sched, K, tol, max_sweeps, &flag);
+  if (threadIdx.x == 0) {
+    if (sweeps > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
+    if (counters) {
+      atomicAdd(&counters[0], 1ULL);
+      atomicAdd(&counters[1], (unsigned long long)sweeps);
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < K; c += nw) {
+    float s2 = 0.f;
+    for (int i = lane; i < K; i += 32) s2 = fmaf(G[c * K + i], G[c * K + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[c] = sqrtf(s2);
+  }
+  __syncthreads();
+  sort_columns<float>(nrm, order, K);
+  __syncthreads();
+  // float64: normalise the leading nvec right vectors
+  for (int k = warp; k < nvec; k += nw) {
+    const int c = order[k];
+    double s2 = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      const double v = (double)W[c * K + i];
+      s2 += v * v;
+    }
+    s2 = warp_sum(s2);
+    const double inv = rsqrt_nr(s2, 2);
+    for (int i = lane; i < K; i += 32) wv[k * K + i] = (double)W[c * K + i] * inv;
+  }
+  __syncthreads();
+  // T w: one thread per output entry, four independent accumulation chains
+  for (int e = threadIdx.x; e < nvec * K; e += blockDim.x) {
+    const int k = e / K, i = e - k * K;
+    const double* trow = Td + i * K;
+    const double* w = wv + k * K;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int cc = 0;
+    for (; cc + 3 < K; cc += 4) {
+      v0 += trow[cc] * w[cc];
+      v1 += trow[cc + 1] * w[cc + 1];
+      v2 += trow[cc + 2] * w[cc + 2];
+      v3 += trow[cc + 3] * w[cc + 3];
+    }
+    for (; cc < K; ++cc) v0 += trow[cc] * w[cc];
+    gx[k * K + i] = (v0 + v1) + (v2 + v3);
+  }
+  __syncthreads();
+  for (int k = warp; k < nvec; k += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < K; i += 32) s2 += gx[k * K + i] * gx[k * K + i];
+    s2 = warp_sum(s2);
+    const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
+    const double inv = th > 0.0 ? rcp_nr(th) : 0.0;
+    for (int i = lane; i < K; i += 32) {
+      Xl[i * K + k] = gx[k * K + i] * inv;
+      Wr[i * K + k] = wv[k * K + i];
+    }
+    if (lane == 0) theta[k] = th;
+    double r2 = 0.0;
+    if (S) {
+      for (int e2 = lane; e2 < b; e2 += 32) {
+        double v = 0.0;
+        for (int d = e2; d < b; ++d) v += S[e2 * b + d] * gx[k * K + (K - b + d)];
+        v *= inv;
+        r2 += v * v;
+      }
+      r2 = warp_sum(r2);
+    }
+    if (lane == 0) res[k] = sqrt(r2);
+  }
+  // remaining triplets (not used by the rank policy): float32 values and vectors
+  for (int e = threadIdx.x; e < (K - nvec) * K; e += blockDim.x) {
+    const int kk = nvec + e / K, i = e % K;
+    const int c = order[kk];
+    const float th = nrm[c];
+    Xl[i * K + kk] = th > 0.f ? (double)(G[c * K + i] / th) : 0.0;
+    Wr[i * K + kk] = (double)W[c * K + i];
+  }
+  for (int kk = nvec + threadIdx.x; kk < K; kk += blockDim.x) {
+    theta[kk] = (double)nrm[order[kk]];
+    res[kk] = INFINITY;
+  }
+}
+
+static int jacobi_threads(int K) {
+  // one pair per JL lanes, at least 8 warps for the epilogue loops
+  int warps = (K / 2 + (32 / JL) - 1) / (32 / JL);
+  if (warps < 8) warps = 8;
+  if (warps > 16) warps = 16;   // launch bound 512 threads (K <= 96 needs at most 12 warps)
+  return 32 * warps;
+}
+
+static size_t sched_bytes(int K) { return (size_t)(K - 1) * (K / 2) * 2; }
+
+template <int JR>
+static void set_smem_attrs(size_t mx64, size_t mxmixed) {
+  cudaFuncSetAttribute(k_jacobi_f64<JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mx64);
+  cudaFuncSetAttribute(k_jacobi_mixed<JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mxmixed);
+}
+
+static bool jacobi_attrs() {
+  static int state = 0;  // 0 unset, 1 ok, 2 failed
+  if (state == 0) {
+    const size_t mx64 =
+        (size_t)(2 * JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
+    const size_t mxm = (size_t)(JMAXK * JMAXK + 2 * JMAXB * JMAXK) * sizeof(double) +
+                       (size_t)(2 * JMAXK * JMAXK + JMAXK) * sizeof(float) + (size_t)JMAXK * sizeof(int) +
+                       sched_bytes(JMAXK);
+    set_smem_attrs<3>(mx64, mxm);
+    set_smem_attrs<6>(mx64, mxm);
+    set_smem_attrs<9>(mx64, mxm);
+    set_smem_attrs<12>(mx64, mxm);
+    state = cudaGetLastError() == cudaSuccess ? 1 : 2;
+  }
+  return state == 1;
+}
+
+int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl, double* Wr,
+                     double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
+                     cudaStream_t st) {
+  if (!jacobi_attrs()) return 0;  // no launch; the caller's cudaGetLastError check reports the failure
+  const size_t smem = (size_t)(2 * K * K + 2 * K) * sizeof(double) + (size_t)K * sizeof(int) + sched_bytes(K);
+  const int thr = jacobi_threads(K);
+  const int rpl = (K + JL - 1) / JL;
+  if (rpl <= 3)
+    k_jacobi_f64<3><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
+  else if (rpl <= 6)
+    k_jacobi_f64<6><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
+  else if (rpl <= 9)
+    k_jacobi_f64<9><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
+  else
+    k_jacobi_f64<12><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
+  return 1;
+}
+
+int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,
+                           double* Wr, double* res, int nvec, double tol, int max_sweeps, unsigned int* err,
+                           unsigned long long* counters, cudaStream_t st) {
+  if (nvec > K) nvec = K;
+  if (nvec > JMAXB) nvec = JMAXB;
+  if (!jacobi_attrs()) return 0;  // no launch; the caller's cudaGetLastError check reports the failure
+  const size_t smem = (size_t)(K * K + 2 * nvec * K) * sizeof(double) + (size_t)(2 * K * K + K) * sizeof(float) +
+                      (size_t)K * sizeof(int) + sched_bytes(K);
+  const int thr = jacobi_threads(K);
+  const int rpl = (K + JL - 1) / JL;
+  const float ft = (float)tol;
+  if (rpl <= 3)
+    k_jacobi_mixed<3><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters);
+  else if (rpl <= 6)
+    k_jacobi_mixed<6><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters);
+  else if (rpl <= 9)
+    k_jacobi_mixed<9><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters);
+  else
+    k_jacobi_mixed<12><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err,
+                                             counters);
+  return 1;
+}
+
+}  // namespace svt
