@@ -21,8 +21,9 @@
  *   - Every call returns an svt_status.  No call aborts, exits or traps the GPU.  After an
  *     error, svt_last_error(ctx) returns a message (or svt_last_error(NULL) for calls that
  *     failed before a context existed).
- *   - Work is issued on the stream given in svt_options.stream (0 = legacy default stream);
- *     calls that return host data synchronise that stream.
+ *   - Work is ordered after everything already queued on svt_options.stream (0 = legacy default
+ *     stream) and everything queued there afterwards runs after the library's work; calls that
+ *     return host data wait for their own work to finish.
  *   - A context is single-threaded.  Distinct contexts may be used concurrently from distinct
  *     threads on distinct streams.
  */
@@ -66,8 +67,11 @@ typedef struct svt_options {
   int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
   double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-10 FP64, 1e-6 FP32) */
   int indices_on_device;  /* rows/cols/M_omega given to svt_create are device pointers */
+  int use_graphs;         /* replay each Lanczos cycle as a captured CUDA graph (default 1) */
   uint64_t seed;          /* seed of the random start columns of the Lanczos blocks */
-  void* stream;           /* cudaStream_t to issue work on; NULL = default stream */
+  void* stream;           /* cudaStream_t the caller orders work on; NULL = default stream.  The
+                             library works on a stream of its own and joins it to this stream with
+                             events at the start and end of every call. */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */

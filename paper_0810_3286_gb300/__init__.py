@@ -70,7 +70,7 @@ class Solver:
 
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
-                 max_cycles: int = 40):
+                 max_cycles: int = 40, use_graphs: bool = True):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -81,6 +81,7 @@ class Solver:
         opt.lanczos_tol = lanczos_tol
         opt.seed = seed
         opt.max_cycles = max_cycles
+        opt.use_graphs = 1 if use_graphs else 0
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda

@@ -44,6 +44,7 @@ class svt_options(ctypes.Structure):
         ("max_cycles", ctypes.c_int),
         ("lanczos_tol", ctypes.c_double),
         ("indices_on_device", ctypes.c_int),
+        ("use_graphs", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
     ]

@@ -56,7 +56,15 @@ struct TmpBufs {
 
 struct svt_ctx {
   int device = 0;
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;        // the library's own non-blocking stream (capturable)
+  cudaStream_t user_st = nullptr;   // the caller's stream (joined at every call)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  struct CycleGraph {
+    int b, J, ycur, twoc;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<CycleGraph> graphs;
   svt_options opt{};
   int64_t m = 0, n = 0, nnz = 0;
   int prec = SVT_FP64;
@@ -220,12 +228,13 @@ static void prof_harvest(svt_ctx* c) {
 }
 
 static svt_status sync_and_check(svt_ctx* c) {
+  unsigned int* herr = reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1);
+  CU(c, cudaMemcpyAsync(herr, c->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaStreamSynchronize(c->st));
   prof_harvest(c);
-  unsigned int e = 0;
-  CU(c, cudaMemcpy(&e, c->err, sizeof e, cudaMemcpyDeviceToHost));
+  const unsigned int e = *herr;
   if (e) {
-    CU(c, cudaMemset(c->err, 0, sizeof e));
+    CU(c, cudaMemsetAsync(c->err, 0, sizeof e, c->st));
     if (e & SVT_DEVERR_INDEX_RANGE) return fail(c, SVT_ERR_ARG, "index outside [0,m) x [0,n)");
     if (e & SVT_DEVERR_DUPLICATE) return fail(c, SVT_ERR_DUP_INDEX, "duplicate (row, col) pair in Omega");
     if (e & SVT_DEVERR_NONFINITE) return fail(c, SVT_ERR_NUMERIC, "NaN or Inf in the residual");
@@ -233,6 +242,31 @@ static svt_status sync_and_check(svt_ctx* c) {
     if (e & SVT_DEVERR_JACOBI) return fail(c, SVT_ERR_NUMERIC, "projected Jacobi SVD did not converge");
     // SVT_DEVERR_CHOL is informational (deflation handled in-kernel)
   }
+  return SVT_OK;
+}
+
+// Orders the library stream after the caller's stream on entry, and the caller's stream after the
+// library stream on exit.
+struct StreamJoin {
+  svt_ctx* c;
+  explicit StreamJoin(svt_ctx* cc) : c(cc) {
+    if (c && c->ev_in) {
+      cudaEventRecord(c->ev_in, c->user_st);
+      cudaStreamWaitEvent(c->st, c->ev_in, 0);
+    }
+  }
+  ~StreamJoin() {
+    if (c && c->ev_out) {
+      cudaEventRecord(c->ev_out, c->st);
+      cudaStreamWaitEvent(c->user_st, c->ev_out, 0);
+    }
+  }
+};
+
+// Device-to-host copy on the library stream, then wait for it.
+static svt_status d2h_sync(svt_ctx* c, void* dst, const void* src, size_t bytes) {
+  CU(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
   return SVT_OK;
 }
 
@@ -313,9 +347,10 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
   return launched(c, l);
 }
 
-// One block Golub-Kahan-Lanczos cycle with full reorthogonalisation from the start block in
-// Vb[0] (n x b).  On return theta/res (host, pinned) hold the Ritz values and residual estimates.
-static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h, const double** res_h) {
+// Issues one block Golub-Kahan-Lanczos cycle with full reorthogonalisation from the start block in
+// Vb[0] (n x b), ending with the projected SVD and the copy of the Ritz values, residual estimates
+// and the orthonormality defect to pinned host memory.  Only stream operations: it can be captured.
+static svt_status issue_cycle(svt_ctx* c, int b, int J) {
   const int m = (int)c->m, n = (int)c->n;
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
@@ -335,8 +370,8 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
     TRY(launched(c, l)); l = 0;
     TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr));
   }
-  // S is written with leading dimension kKMax by orth_small; the small SVD reads it as b x b with
-  // leading dimension b, so compact it first.
+  // S is written with leading dimension kKMax; the projected SVD reads it as b x b with leading
+  // dimension b, so compact it first.
   CU(c, cudaMemcpy2DAsync(c->Rkeep, b * sizeof(double), c->S, kKMax * sizeof(double), b * sizeof(double), b,
                           cudaMemcpyDeviceToDevice, c->st));
   // one-sided Jacobi stops when every column pair is orthogonal to the rounding level of a length-K
@@ -350,13 +385,59 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
                                   c->dcount, c->st);
   });
   TRY(launched(c, l));
+  CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax + 1, c->dcount + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return SVT_OK;
+}
+
+// Captures issue_cycle for this (b, J, Y buffer, correction mode) once and replays it afterwards:
+// one graph launch instead of ~60 kernel launches per cycle.
+static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
+  const int twoc = c->two_corrections ? 1 : 0;
+  for (auto& g : c->graphs)
+    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc) {
+      CU(c, cudaGraphLaunch(g.exec, c->st));
+      c->launches += g.launches;
+      return SVT_OK;
+    }
+  const int64_t l0 = c->launches;
+  CU(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+  svt_status s = issue_cycle(c, b, J);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+  const int64_t nl = c->launches - l0;
+  c->launches = l0;
+  if (s != SVT_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    (void)cudaGetLastError();
+    if (s != SVT_OK) return s;
+    return fail(c, SVT_ERR_CUDA, "stream capture of the Lanczos cycle failed: %s", cudaGetErrorString(e));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
+  }
+  c->graphs.push_back({b, J, c->ycur, twoc, exec, nl});
+  CU(c, cudaGraphLaunch(exec, c->st));
+  c->launches += nl;
+  return SVT_OK;
+}
+
+// One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
+static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h, const double** res_h) {
+  if (c->opt.use_graphs && c->prof_mask == 0) {
+    TRY(run_cycle_graph(c, b, J));
+  } else {
+    TRY(issue_cycle(c, b, J));
+  }
   c->last_spmm += 2 * J;
   c->total_spmm += 2 * J;
   c->last_cycles += 1;
   c->total_cycles += 1;
-  CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
-  CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
-  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax + 1, c->dcount + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   TRY(sync_and_check(c));
   {
     double defect = 0.0;
@@ -523,6 +604,8 @@ extern "C" int64_t svt_kernel_launches(const svt_ctx* ctx) { return ctx ? ctx->l
 extern "C" void svt_destroy(svt_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (auto& r : c->prof_pending) {
@@ -532,6 +615,9 @@ extern "C" void svt_destroy(svt_ctx* c) {
   for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->st) cudaStreamDestroy(c->st);
   delete c;
 }
 
@@ -557,11 +643,14 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
   TRY(launched(c, l)); l = 0;
   TRY(sync_and_check(c));
   int32_t mx = 0;
-  CU(c, cudaMemcpy(&mx, maxseg, sizeof mx, cudaMemcpyDeviceToHost));
+  TRY(d2h_sync(c, &mx, maxseg, sizeof mx));
   if (mx > segment_smem_capacity()) {
     host_ptr = new (std::nothrow) int32_t[m + 1];
     if (!host_ptr) return fail(c, SVT_ERR_OOM, "host allocation failed");
-    CU(c, cudaMemcpy(host_ptr, c->row_ptr, sizeof(int32_t) * (m + 1), cudaMemcpyDeviceToHost));
+    if (d2h_sync(c, host_ptr, c->row_ptr, sizeof(int32_t) * (m + 1)) != SVT_OK) {
+      delete[] host_ptr;
+      return SVT_ERR_CUDA;
+    }
     int32_t* scratch = nullptr;
     int L = 1;
     while (L < mx) L <<= 1;
@@ -592,11 +681,14 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
   l += launch_max_segment(c->col_ptr, n, maxseg, c->st);
   TRY(launched(c, l)); l = 0;
   TRY(sync_and_check(c));
-  CU(c, cudaMemcpy(&mx, maxseg, sizeof mx, cudaMemcpyDeviceToHost));
+  TRY(d2h_sync(c, &mx, maxseg, sizeof mx));
   if (mx > segment_smem_capacity()) {
     host_ptr = new (std::nothrow) int32_t[n + 1];
     if (!host_ptr) return fail(c, SVT_ERR_OOM, "host allocation failed");
-    CU(c, cudaMemcpy(host_ptr, c->col_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+    if (d2h_sync(c, host_ptr, c->col_ptr, sizeof(int32_t) * (n + 1)) != SVT_OK) {
+      delete[] host_ptr;
+      return SVT_ERR_CUDA;
+    }
     int32_t* scratch = nullptr;
     int L = 1;
     while (L < mx) L <<= 1;
@@ -615,9 +707,78 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
   TRY(launched(c, l));
   TRY(sync_and_check(c));
   double ss = 0.0;
-  CU(c, cudaMemcpy(&ss, c->dscal, sizeof ss, cudaMemcpyDeviceToHost));
+  TRY(d2h_sync(c, &ss, c->dscal, sizeof ss));
   c->normF = std::sqrt(ss);
   return SVT_OK;
+}
+
+// Allocations, input staging and the Omega storage build of svt_create.  Local temporaries are
+// released when this returns, before svt_create destroys a failed context.
+static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* cols, const double* M_omega) {
+  const int64_t m = c->m, n = c->n, nnz = c->nnz;
+  StreamJoin join(c);
+  TRY(dalloc_t(c, &c->err, 4));
+  CU(c, cudaMemsetAsync(c->err, 0, 4, c->st));
+  TRY(dalloc_t(c, &c->row_ptr, m + 1));
+  TRY(dalloc_t(c, &c->col_idx, nnz));
+  TRY(dalloc_t(c, &c->col_ptr, n + 1));
+  TRY(dalloc_t(c, &c->row_idx, nnz));
+  TRY(dalloc_t(c, &c->csc_to_csr, nnz));
+  TRY(dalloc_t(c, &c->csr_to_csc, nnz));
+  TRY(dalloc(c, &c->Mv, nnz * c->vbytes));
+  for (int i = 0; i < 2; ++i) {
+    TRY(dalloc(c, &c->Ycsr[i], nnz * c->vbytes));
+    TRY(dalloc(c, &c->Ycsc[i], nnz * c->vbytes));
+  }
+  const int cap = kMaxRankCap + 1;
+  TRY(dalloc_t(c, &c->Ut, (size_t)m * cap));
+  TRY(dalloc_t(c, &c->Uf, (size_t)m * cap));
+  TRY(dalloc_t(c, &c->Vf, (size_t)n * cap));
+  TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
+  TRY(dalloc_t(c, &c->Ub, (size_t)m * (kKMax + kBMax)));
+  TRY(dalloc_t(c, &c->Vb, (size_t)n * (kKMax + kBMax)));
+  TRY(dalloc_t(c, &c->T, (size_t)kKMax * kKMax));
+  TRY(dalloc_t(c, &c->S, (size_t)kKMax * kBMax));
+  TRY(dalloc_t(c, &c->theta, kKMax));
+  TRY(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
+  TRY(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
+  TRY(dalloc_t(c, &c->res, kKMax));
+  TRY(dalloc_t(c, &c->G1, 128 * 32));
+  TRY(dalloc_t(c, &c->G2, 128 * 32));
+  TRY(dalloc_t(c, &c->G3, 128 * 32));
+  TRY(dalloc_t(c, &c->R1, kBMax * kBMax));
+  TRY(dalloc_t(c, &c->R2, kBMax * kBMax));
+  TRY(dalloc_t(c, &c->dinv, kBMax));
+  TRY(dalloc_t(c, &c->dcount, 8));
+  CU(c, cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->st));
+  // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
+  TRY(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
+  TRY(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
+  TRY(dalloc_t(c, &c->scale, 64));
+  TRY(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
+  TRY(dalloc_t(c, &c->dscal, 16));
+  CU(c, cudaMallocHost((void**)&c->h_pin, sizeof(double) * 4 * kKMax));
+  CU(c, cudaEventCreate(&c->ev0));
+  CU(c, cudaEventCreate(&c->ev1));
+  // inputs on the device
+  const int32_t *rows_d = rows, *cols_d = cols;
+  const double* M_d = M_omega;
+  TmpBufs staged(c->st);
+  if (!c->opt.indices_on_device) {
+    int32_t *r2, *c2;
+    double* m2;
+    if (!staged.get(&r2, nnz) || !staged.get(&c2, nnz) || !staged.get(&m2, nnz))
+      return fail(c, SVT_ERR_OOM, "device allocation of the input copy failed");
+    CU(c, cudaMemcpyAsync(r2, rows, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c2, cols, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st));
+    CU(c, cudaMemcpyAsync(m2, M_omega, sizeof(double) * nnz, cudaMemcpyHostToDevice, c->st));
+    rows_d = r2; cols_d = c2; M_d = m2;
+  }
+  TRY(build_structure(c, rows_d, cols_d, M_d));
+  // Y^0 = 0 until configured
+  CU(c, cudaMemsetAsync(c->Ycsr[0], 0, nnz * c->vbytes, c->st));
+  CU(c, cudaMemsetAsync(c->Ycsc[0], 0, nnz * c->vbytes, c->st));
+  return sync_and_check(c);
 }
 
 extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
@@ -642,107 +803,32 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   c->m = m; c->n = n; c->nnz = nnz;
   c->prec = o.precision;
   c->vbytes = c->prec == SVT_FP64 ? 8 : 4;
-  c->st = (cudaStream_t)o.stream;
-  auto bail = [&](svt_status s) {
+  c->user_st = (cudaStream_t)o.stream;
+  svt_status s = SVT_OK;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    s = fail(c, SVT_ERR_CUDA, "no CUDA device");
+  } else if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    s = fail(c, SVT_ERR_CUDA, "stream/event creation failed");
+  } else if (init_jacobi_attributes() != 0) {
+    s = fail(c, SVT_ERR_CUDA, "setting the shared-memory limit of the projected-SVD kernels failed");
+  } else {
+    s = create_body(c, rows, cols, M_omega);
+  }
+  if (s != SVT_OK) {
+    (void)cudaGetLastError();
     g_create_error = c->last_error;
     svt_destroy(c);
     return s;
-  };
-  if (cudaGetDevice(&c->device) != cudaSuccess) {
-    (void)cudaGetLastError();
-    fail(c, SVT_ERR_CUDA, "no CUDA device");
-    return bail(SVT_ERR_CUDA);
   }
-  svt_status s = SVT_OK;
-#define A(expr) do { s = (expr); if (s != SVT_OK) return bail(s); } while (0)
-  A(dalloc_t(c, &c->err, 4));
-  if (cudaMemsetAsync(c->err, 0, 4, c->st) != cudaSuccess) { fail(c, SVT_ERR_CUDA, "memset"); return bail(SVT_ERR_CUDA); }
-  A(dalloc_t(c, &c->row_ptr, m + 1));
-  A(dalloc_t(c, &c->col_idx, nnz));
-  A(dalloc_t(c, &c->col_ptr, n + 1));
-  A(dalloc_t(c, &c->row_idx, nnz));
-  A(dalloc_t(c, &c->csc_to_csr, nnz));
-  A(dalloc_t(c, &c->csr_to_csc, nnz));
-  A(dalloc(c, &c->Mv, nnz * c->vbytes));
-  for (int i = 0; i < 2; ++i) {
-    A(dalloc(c, &c->Ycsr[i], nnz * c->vbytes));
-    A(dalloc(c, &c->Ycsc[i], nnz * c->vbytes));
-  }
-  const int cap = kMaxRankCap + 1;
-  A(dalloc_t(c, &c->Ut, (size_t)m * cap));
-  A(dalloc_t(c, &c->Uf, (size_t)m * cap));
-  A(dalloc_t(c, &c->Vf, (size_t)n * cap));
-  A(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
-  A(dalloc_t(c, &c->Ub, (size_t)m * (kKMax + kBMax)));
-  A(dalloc_t(c, &c->Vb, (size_t)n * (kKMax + kBMax)));
-  A(dalloc_t(c, &c->T, (size_t)kKMax * kKMax));
-  A(dalloc_t(c, &c->S, (size_t)kKMax * kBMax));
-  A(dalloc_t(c, &c->theta, kKMax));
-  A(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
-  A(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
-  A(dalloc_t(c, &c->res, kKMax));
-  A(dalloc_t(c, &c->G1, 128 * 32));
-  A(dalloc_t(c, &c->G2, 128 * 32));
-  A(dalloc_t(c, &c->G3, 128 * 32));
-  A(dalloc_t(c, &c->R1, kBMax * kBMax));
-  A(dalloc_t(c, &c->R2, kBMax * kBMax));
-  A(dalloc_t(c, &c->dinv, kBMax));
-  A(dalloc_t(c, &c->dcount, 8));
-  if (cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->st) != cudaSuccess) {
-    fail(c, SVT_ERR_CUDA, "memset");
-    return bail(SVT_ERR_CUDA);
-  }
-  // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
-  A(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
-  A(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
-  A(dalloc_t(c, &c->scale, 64));
-  A(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
-  A(dalloc_t(c, &c->dscal, 16));
-  if (cudaMallocHost((void**)&c->h_pin, sizeof(double) * 4 * kKMax) != cudaSuccess) {
-    (void)cudaGetLastError();
-    fail(c, SVT_ERR_OOM, "cudaMallocHost failed");
-    return bail(SVT_ERR_OOM);
-  }
-  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
-    (void)cudaGetLastError();
-    fail(c, SVT_ERR_CUDA, "cudaEventCreate failed");
-    return bail(SVT_ERR_CUDA);
-  }
-  // inputs on the device
-  const int32_t *rows_d = rows, *cols_d = cols;
-  const double* M_d = M_omega;
-  TmpBufs staged(c->st);
-  if (!o.indices_on_device) {
-    int32_t *r2, *c2;
-    double* m2;
-    if (!staged.get(&r2, nnz) || !staged.get(&c2, nnz) || !staged.get(&m2, nnz)) {
-      fail(c, SVT_ERR_OOM, "device allocation of the input copy failed");
-      return bail(SVT_ERR_OOM);
-    }
-    if (cudaMemcpyAsync(r2, rows, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
-        cudaMemcpyAsync(c2, cols, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess ||
-        cudaMemcpyAsync(m2, M_omega, sizeof(double) * nnz, cudaMemcpyHostToDevice, c->st) != cudaSuccess) {
-      (void)cudaGetLastError();
-      fail(c, SVT_ERR_CUDA, "host-to-device copy of Omega failed");
-      return bail(SVT_ERR_CUDA);
-    }
-    rows_d = r2; cols_d = c2; M_d = m2;
-  }
-  A(build_structure(c, rows_d, cols_d, M_d));
-  // Y^0 = 0 until configured
-  if (cudaMemsetAsync(c->Ycsr[0], 0, nnz * c->vbytes, c->st) != cudaSuccess ||
-      cudaMemsetAsync(c->Ycsc[0], 0, nnz * c->vbytes, c->st) != cudaSuccess) {
-    fail(c, SVT_ERR_CUDA, "memset failed");
-    return bail(SVT_ERR_CUDA);
-  }
-  A(sync_and_check(c));
-#undef A
   *out = c;
   return SVT_OK;
 }
 
 extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double eps, int max_rank, int64_t k0) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (max_rank < 1 || max_rank > kMaxRankCap)
     return fail(c, SVT_ERR_ARG, "max_rank must be in [1, %d]", kMaxRankCap);
   const double mn = (double)c->m * (double)c->n;
@@ -775,6 +861,7 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
 
 extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
   CU(c, cudaEventRecord(c->ev0, c->st));
   int r = 0;
@@ -811,6 +898,7 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
 
 extern "C" svt_status svt_solve(svt_ctx* c, double tau, double delta, double eps, int max_rank, svt_result* out) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   cudaEvent_t e0, e1;
   CU(c, cudaEventCreate(&e0));
   CU(c, cudaEventCreate(&e1));
@@ -857,6 +945,7 @@ extern "C" svt_status svt_get_rank(const svt_ctx* c, int* r) {
 
 extern "C" svt_status svt_get_factors(svt_ctx* c, double* U, double* d, double* V, int capacity_r) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (capacity_r < c->r) return fail(c, SVT_ERR_ARG, "capacity_r %d < rank %d", capacity_r, c->r);
   const int r = c->r;
   if (r == 0) return SVT_OK;
@@ -873,6 +962,7 @@ extern "C" svt_status svt_get_factors(svt_ctx* c, double* U, double* d, double* 
 
 extern "C" svt_status svt_get_Y(svt_ctx* c, double* y) {
   if (!c || !y) return SVT_ERR_ARG;
+  StreamJoin join(c);
   double* tmp = nullptr;
   TRY(dalloc_t(c, &tmp, c->nnz));
   TRY(launched(c, launch_store_values(c->prec, ycur_csr(c), tmp, c->nnz, c->st)));
@@ -885,6 +975,7 @@ extern "C" svt_status svt_get_Y(svt_ctx* c, double* y) {
 
 extern "C" svt_status svt_set_Y(svt_ctx* c, const double* y) {
   if (!c || !y) return SVT_ERR_ARG;
+  StreamJoin join(c);
   double* tmp = nullptr;
   TRY(dalloc_t(c, &tmp, c->nnz));
   CU(c, cudaMemcpyAsync(tmp, y, sizeof(double) * c->nnz, cudaMemcpyHostToDevice, c->st));
@@ -898,6 +989,7 @@ extern "C" svt_status svt_set_Y(svt_ctx* c, const double* y) {
 extern "C" svt_status svt_get_structure(svt_ctx* c, int32_t* row_ptr, int32_t* col_idx, int32_t* col_ptr,
                                         int32_t* row_idx, int32_t* csc_to_csr) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (row_ptr) CU(c, cudaMemcpyAsync(row_ptr, c->row_ptr, 4 * (c->m + 1), cudaMemcpyDeviceToHost, c->st));
   if (col_idx) CU(c, cudaMemcpyAsync(col_idx, c->col_idx, 4 * c->nnz, cudaMemcpyDeviceToHost, c->st));
   if (col_ptr) CU(c, cudaMemcpyAsync(col_ptr, c->col_ptr, 4 * (c->n + 1), cudaMemcpyDeviceToHost, c->st));
@@ -909,6 +1001,7 @@ extern "C" svt_status svt_get_structure(svt_ctx* c, int32_t* row_ptr, int32_t* c
 
 extern "C" svt_status svt_shrink(svt_ctx* c, double tau, int* r_out, double* sigma) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (tau <= 0) tau = c->tau;
   if (!(tau > 0)) return fail(c, SVT_ERR_ARG, "tau must be positive (or configured)");
   if (c->max_rank < 1) c->max_rank = kMaxRankCap;
@@ -925,6 +1018,7 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 extern "C" svt_status svt_apply_Y(svt_ctx* c, const double* V, int b, double* W) {
   if (!c || !V || !W) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(V) || !aligned16(W)) return fail(c, SVT_ERR_ARG, "V and W must be 16-byte aligned");
   return launched(c, prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, (int)c->m, (int)c->n, b), [&] {
@@ -934,6 +1028,7 @@ extern "C" svt_status svt_apply_Y(svt_ctx* c, const double* V, int b, double* W)
 
 extern "C" svt_status svt_apply_Yt(svt_ctx* c, const double* U, int b, double* Z) {
   if (!c || !U || !Z) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(U) || !aligned16(Z)) return fail(c, SVT_ERR_ARG, "U and Z must be 16-byte aligned");
   return launched(c, prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, (int)c->n, (int)c->m, b), [&] {
@@ -944,6 +1039,7 @@ extern "C" svt_status svt_apply_Yt(svt_ctx* c, const double* U, int b, double* Z
 extern "C" svt_status svt_sddmm_update(svt_ctx* c, const double* Ut, const double* V, int r, double delta,
                                        const double* y_in, double* y_out, double* res2) {
   if (!c || !y_in || !y_out || !res2) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (r < 0 || r > 64 || (r > 0 && (!Ut || !V))) return fail(c, SVT_ERR_ARG, "need 0 <= r <= 64 and factors");
   // the kernel works in the context's value type: stage float64 in/out through the Y buffers
   const int nxt = 1 - c->ycur;
@@ -1059,6 +1155,7 @@ static size_t state_bytes(const svt_ctx* c) {
 
 extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   if (!c || !bytes) return SVT_ERR_ARG;
+  StreamJoin join(c);
   const size_t need = state_bytes(c);
   if (!buf) { *bytes = need; return SVT_OK; }
   if (*bytes < need) return fail(c, SVT_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
@@ -1082,6 +1179,7 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
 
 extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) {
   if (!c || !buf) return SVT_ERR_ARG;
+  StreamJoin join(c);
   if (bytes < sizeof(StateHeader)) return fail(c, SVT_ERR_ARG, "state buffer too small");
   StateHeader h;
   std::memcpy(&h, buf, sizeof h);
@@ -1121,6 +1219,7 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
 // ------------------------------------------------------------------------------------------------
 extern "C" svt_status svt_set_profile(svt_ctx* c, unsigned int class_mask) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   CU(c, cudaStreamSynchronize(c->st));
   prof_harvest(c);
   c->prof_mask = class_mask;
@@ -1134,6 +1233,7 @@ extern "C" svt_status svt_set_profile(svt_ctx* c, unsigned int class_mask) {
 
 extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms, double* bytes) {
   if (!c) return SVT_ERR_ARG;
+  StreamJoin join(c);
   CU(c, cudaStreamSynchronize(c->st));
   prof_harvest(c);
   for (int i = 0; i < SVT_PROF_CLASSES; ++i) {
@@ -1147,8 +1247,8 @@ extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms,
 extern "C" svt_status svt_get_counters(svt_ctx* c, double* out, int n) {
   if (!c || !out || n < 0) return SVT_ERR_ARG;
   unsigned long long dc[8] = {0};
-  CU(c, cudaStreamSynchronize(c->st));
-  CU(c, cudaMemcpy(dc, c->dcount, sizeof dc, cudaMemcpyDeviceToHost));
+  StreamJoin join(c);
+  TRY(d2h_sync(c, dc, c->dcount, sizeof dc));
   double maxdef = 0.0;
   std::memcpy(&maxdef, &dc[3], sizeof maxdef);
   const double v[8] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],

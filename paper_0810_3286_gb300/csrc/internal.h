@@ -91,6 +91,10 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, do
                      double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
                      cudaStream_t st);
 
+// Sets the dynamic shared-memory limits of the projected-SVD kernels (call before any stream
+// capture); returns 0 on success.
+int init_jacobi_attributes();
+
 // Float32-rotation Jacobi with float64 Ritz values for the leading nvec triplets (see dense.cu).
 int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,
                            double* Wr, double* res, int nvec, double tol, int max_sweeps, unsigned int* err,

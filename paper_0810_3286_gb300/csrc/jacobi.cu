@@ -365,7 +365,10 @@ static void set_smem_attrs(size_t mx64, size_t mxmixed) {
   cudaFuncSetAttribute(k_jacobi_mixed<JR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mxmixed);
 }
 
-static bool jacobi_attrs() {
+bool jacobi_attrs();
+int init_jacobi_attributes() { return jacobi_attrs() ? 0 : 1; }
+
+bool jacobi_attrs() {
   static int state = 0;  // 0 unset, 1 ok, 2 failed
   if (state == 0) {
     const size_t mx64 =

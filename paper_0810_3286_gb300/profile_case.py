@@ -24,6 +24,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--lanczos-steps", type=int, default=3)
     ap.add_argument("--verbose", action="store_true", help="print every step's record")
+    ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one (no CUDA graphs)")
     args = ap.parse_args()
     import torch
     from paper_0810_3286_gb300 import Solver, build
@@ -34,7 +35,8 @@ def main():
     rows = torch.from_numpy(p.rows).cuda()
     cols = torch.from_numpy(p.cols).cuda()
     vals = torch.from_numpy(p.vals).cuda()
-    s = Solver(p.n1, p.n2, rows, cols, vals, precision=args.precision, lanczos_steps=args.lanczos_steps)
+    s = Solver(p.n1, p.n2, rows, cols, vals, precision=args.precision, lanczos_steps=args.lanczos_steps,
+               use_graphs=not args.no_graphs)
     s.configure(p.tau_default(), p.delta_default(), 1e-4, 27)
     info = None
     for _ in range(args.iters):
