@@ -267,6 +267,36 @@ svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* 
  */
 svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);
 
+/*
+ * Allocation-free variant of svt_sddmm_update (the paper has no counterpart: this is a deployment
+ * convenience).  Some callers cannot call cudaMalloc -- a process whose device memory is already
+ * handed to its own pool (a framework's caching allocator, a server with a fixed memory budget)
+ * or a latency-critical loop that cannot afford the implicit device synchronisation of
+ * cudaMalloc/cudaFree.  This call allocates nothing and needs no context: the caller passes the
+ * row-major storage of Omega and all inputs and outputs as device pointers, and the only scratch
+ * (one partial sum per 64 rows plus the total) is a file-scope device array of 4096 doubles
+ * (32 KB) that every GPU which loads libsvt holds until the process exits.
+ *   m, n, nnz           dimensions; 1 <= m <= 262080 (larger m: SVT_ERR_ARG, the scratch holds at
+ *                       most 4095 partial sums), n >= 1, 0 <= nnz < 2^31
+ *   row_ptr, col_idx    row-major storage of Omega (m + 1 and nnz int32, columns increasing)
+ *   M                   nnz sampled values (float64, row-major order)
+ *   Ut, V               m x r and n x r float64 factors (Ut = U diag(d)), 0 <= r <= 64
+ *   y_in, y_out         nnz float64 each, distinct buffers: y_out = y_in + delta (M - x)
+ *   res2                host pointer: sum over Omega of (M - x)^2
+ *   stream              cudaStream_t (NULL = default stream); the call waits for its own work
+ * Arithmetic is float64, the kernel of svt_sddmm_update on a float64 context.
+ * The first call on each device looks up the device address of the scratch array (once per
+ * device, with that device current); make that first call before any stream capture.  Every call
+ * on a device shares the array and the array keeps the last call's contents; each call writes
+ * every entry it reads, so nothing needs clearing, but calls whose device work overlaps (for
+ * instance on different streams) race on it.  Errors: SVT_ERR_ARG, SVT_ERR_CUDA, SVT_ERR_NUMERIC;
+ * the message is in svt_noalloc_last_error().
+ */
+svt_status svt_sddmm_update_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                                    const double* M, const double* Ut, const double* V, int r, double delta,
+                                    const double* y_in, double* y_out, double* res2, void* stream);
+const char* svt_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

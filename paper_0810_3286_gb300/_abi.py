@@ -113,6 +113,9 @@ PROTOTYPES = {
     "svt_set_profile": (ctypes.c_int, [_ctxp, ctypes.c_uint]),
     "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp]),
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
+    "svt_sddmm_update_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
+                                                _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _dp, _vp]),
+    "svt_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "deflated_columns",

@@ -116,6 +116,11 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
                         const double* V, int r, int n_rows, double delta, double* partial, double* res2,
                         unsigned int* err, cudaStream_t st);
 int sddmm_partial_doubles();
+// The same fused kernel (float64 values, no column-major copy) on `blocks` CTAs of 256 threads,
+// one partial sum per CTA in `partial`, the fixed-order total in *res2 (device).
+int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, const double* M, const double* y_in,
+                             double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
+                             int blocks, double* partial, double* res2, cudaStream_t st);
 
 // y[p] = alpha * M[p] for the value type of `precision`; also writes the CSC copy via csr_to_csc.
 int launch_scale_values(int precision, const void* M, double alpha, void* y, void* y_csc, const int32_t* csr_to_csc,

@@ -294,3 +294,28 @@ int launch_store_values(int precision, const void* y, double* dst, long long nnz
 }
 
 }  // namespace svt
+
+namespace svt {
+
+// Same fused kernel with a caller-chosen grid and partial-sum buffer (one partial per CTA), for the
+// entry point that works without device allocations.
+int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, const double* M, const double* y_in,
+                             double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
+                             int blocks, double* partial, double* res2, cudaStream_t st) {
+  if (r <= 16)
+    k_sddmm_update<double, double, 16><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
+                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
+                                                                        nullptr);
+  else if (r <= 32)
+    k_sddmm_update<double, double, 32><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
+                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
+                                                                        nullptr);
+  else
+    k_sddmm_update<double, double, 64><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
+                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
+                                                                        nullptr);
+  k_sum_fixed<<<1, 1024, 0, st>>>(partial, blocks, res2);
+  return 2;
+}
+
+}  // namespace svt
