@@ -59,10 +59,13 @@ struct svt_ctx {
   cudaStream_t st = nullptr;        // the library's own non-blocking stream (capturable)
   cudaStream_t user_st = nullptr;   // the caller's stream (joined at every call)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  struct ProfNode { int cls; double bytes; cudaEvent_t a, b; };
   struct CycleGraph {
     int b, J, ycur, twoc;
+    unsigned int prof_mask;
     cudaGraphExec_t exec;
     int64_t launches;
+    std::vector<ProfNode> prof;   // event pairs recorded by the graph's own event-record nodes
   };
   std::vector<CycleGraph> graphs;
   svt_options opt{};
@@ -101,7 +104,7 @@ struct svt_ctx {
   double *T = nullptr, *S = nullptr, *theta = nullptr, *Xl = nullptr, *Wr = nullptr, *res = nullptr;
   double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
   double *Rkeep = nullptr, *scale = nullptr;
-  bool two_corrections = false;           // set once an orthonormality defect above 1e-7 was seen
+  bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
   double* R2 = nullptr;                   // b x b product of the first correction and R1
   unsigned long long* dcount = nullptr;   // device counters: [0] Jacobi calls [1] Jacobi sweeps
                                           // [2] deflated columns [3] max orthonormality defect (bits)
@@ -113,7 +116,7 @@ struct svt_ctx {
   // per-kernel-class profile (CUDA events around launches of the classes in prof_mask)
   unsigned int prof_mask = 0;
   std::vector<cudaEvent_t> prof_pool;
-  struct ProfRec { int cls; double bytes; cudaEvent_t a, b; };
+  struct ProfRec { int cls; double bytes; cudaEvent_t a, b; bool graph_owned; };
   std::vector<ProfRec> prof_pending;
   double prof_ms[SVT_PROF_CLASSES] = {0};
   double prof_bytes[SVT_PROF_CLASSES] = {0};
@@ -203,10 +206,15 @@ static int prof_launch(svt_ctx* c, int cls, double bytes, F&& f) {
   if (!(c->prof_mask & (1u << cls))) return f();
   cudaEvent_t a = prof_event(c), b = prof_event(c);
   if (!a || !b) return f();
-  cudaEventRecord(a, c->st);
+  // during stream capture the records must become external event-record nodes of the graph, so
+  // that they are real timestamps on every replay
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->st, &cs);
+  const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaEventRecordWithFlags(a, c->st, flags);
   int n = f();
-  cudaEventRecord(b, c->st);
-  c->prof_pending.push_back({cls, bytes, a, b});
+  cudaEventRecordWithFlags(b, c->st, flags);
+  c->prof_pending.push_back({cls, bytes, a, b, false});
   return n;
 }
 
@@ -221,8 +229,10 @@ static void prof_harvest(svt_ctx* c) {
     } else {
       (void)cudaGetLastError();
     }
-    c->prof_pool.push_back(r.a);
-    c->prof_pool.push_back(r.b);
+    if (!r.graph_owned) {
+      c->prof_pool.push_back(r.a);
+      c->prof_pool.push_back(r.b);
+    }
   }
   c->prof_pending.clear();
 }
@@ -396,21 +406,35 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J) {
 static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
   const int twoc = c->two_corrections ? 1 : 0;
   for (auto& g : c->graphs)
-    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc) {
+    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.prof_mask == c->prof_mask) {
       CU(c, cudaGraphLaunch(g.exec, c->st));
       c->launches += g.launches;
+      // the graph's event-record nodes fire again on every replay: harvest them at the next sync
+      for (auto& pn : g.prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.a, pn.b, true});
       return SVT_OK;
     }
   const int64_t l0 = c->launches;
+  const size_t p0 = c->prof_pending.size();
   CU(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
   svt_status s = issue_cycle(c, b, J);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->st, &graph);
   const int64_t nl = c->launches - l0;
   c->launches = l0;
+  // event pairs recorded during capture belong to the graph (they only fire when it is replayed)
+  std::vector<svt_ctx::ProfNode> prof;
+  for (size_t i = p0; i < c->prof_pending.size(); ++i) {
+    const auto& r = c->prof_pending[i];
+    prof.push_back({r.cls, r.bytes, r.a, r.b});
+  }
+  c->prof_pending.resize(p0);
   if (s != SVT_OK || e != cudaSuccess) {
     if (graph) cudaGraphDestroy(graph);
     (void)cudaGetLastError();
+    for (auto& pn : prof) {
+      c->prof_pool.push_back(pn.a);
+      c->prof_pool.push_back(pn.b);
+    }
     if (s != SVT_OK) return s;
     return fail(c, SVT_ERR_CUDA, "stream capture of the Lanczos cycle failed: %s", cudaGetErrorString(e));
   }
@@ -421,15 +445,16 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
     (void)cudaGetLastError();
     return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
   }
-  c->graphs.push_back({b, J, c->ycur, twoc, exec, nl});
+  c->graphs.push_back({b, J, c->ycur, twoc, c->prof_mask, exec, nl, prof});
   CU(c, cudaGraphLaunch(exec, c->st));
   c->launches += nl;
+  for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.a, pn.b, true});
   return SVT_OK;
 }
 
 // One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
 static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h, const double** res_h) {
-  if (c->opt.use_graphs && c->prof_mask == 0) {
+  if (c->opt.use_graphs) {
     TRY(run_cycle_graph(c, b, J));
   } else {
     TRY(issue_cycle(c, b, J));
@@ -442,7 +467,7 @@ static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h
   {
     double defect = 0.0;
     std::memcpy(&defect, c->h_pin + 3 * kKMax + 1, sizeof defect);
-    if (defect > 1e-7) c->two_corrections = true;
+    if (defect > 1e-6) c->two_corrections = true;
   }
   *theta_h = c->h_pin;
   *res_h = c->h_pin + kKMax;
@@ -604,11 +629,18 @@ extern "C" int64_t svt_kernel_launches(const svt_ctx* ctx) { return ctx ? ctx->l
 extern "C" void svt_destroy(svt_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
-  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : c->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    for (auto& pn : g.prof) {
+      cudaEventDestroy(pn.a);
+      cudaEventDestroy(pn.b);
+    }
+  }
   c->graphs.clear();
   for (void* p : c->allocations) cudaFree(p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (auto& r : c->prof_pending) {
+    if (r.graph_owned) continue;
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }

@@ -46,8 +46,9 @@ template <>
 struct Rot<float> {
   // zeta = (beta - alpha) / (2 gamma), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1+t^2)
   static __device__ __forceinline__ void params(float al, float be, float ga, float& c, float& s) {
-    float zeta = __fdividef(be - al, 2.f * ga);
-    float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+    const float zeta = __fdividef(be - al, 2.f * ga);
+    const float h = __fsqrt_rn(fmaf(zeta, zeta, 1.f));
+    const float t = copysignf(__frcp_rn(fabsf(zeta) + h), zeta);
     c = rsqrtf(fmaf(t, t, 1.f));
     s = c * t;
   }
@@ -83,9 +84,14 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
   const int gl = lane & (JL - 1);                 // lane inside the pair group
   const int gsub = lane / JL;                     // pair slot inside the warp
   const int npairs = K / 2;
+  __shared__ float sweep_max;   // largest |cos| between a rotated pair in this sweep
   int sweep = 0;
+  bool final_sweep = false;
   for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) *flag = 0;
+    if (threadIdx.x == 0) {
+      *flag = 0;
+      sweep_max = 0.f;
+    }
     __syncthreads();
     for (int round = 0; round < K - 1; ++round) {
       const unsigned char* rs = sched + 2 * round * npairs;
@@ -113,7 +119,9 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
           be += shfl_grp(be, o);
           ga += shfl_grp(ga, o);
         }
-        if (has && ga != R(0) && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+        const R nab = sqrt(al) * sqrt(be);
+        if (has && ga != R(0) && fabs(ga) > tol * nab) {
+          if (gl == 0) atomicMax(reinterpret_cast<int*>(&sweep_max), __float_as_int((float)(fabs(ga) / nab)));
           R c, s;
           Rot<R>::params(al, be, ga, c, s);
           R* wp = W + p * K;
@@ -134,7 +142,10 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
       }
       __syncthreads();
     }
-    if (!*flag) break;
+    if (!*flag || final_sweep) break;
+    // quadratic convergence: once every rotated pair had |cos| <= sqrt(tol), the next sweep leaves
+    // them at the tol level, so it is the last one (no further verification sweep)
+    final_sweep = sweep_max <= (float)sqrt(tol);
     __syncthreads();
   }
   return sweep + 1;

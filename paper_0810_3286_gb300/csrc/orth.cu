@@ -231,27 +231,25 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
 }
 
 // ------------------------------------------------------------------------------------------------
-// Cholesky with deflation of the b x b block A of G2 (one warp, lane t owns column t).
+// Cholesky with deflation of the b x b block A of G2 (one warp, lane t owns column t; B = compile-
+// time block size so every loop has exact bounds).  Pivots: float32 reciprocal square root refined
+// by one float64 Newton step (relative error ~1e-14; the float32 seed alone would leave errors of
+// 1e-7 times the condition number of the Gram, which reaches 1e3 - 1e4 in Krylov blocks).
 // ------------------------------------------------------------------------------------------------
+template <int B>
 __global__ void __launch_bounds__(32)
-k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, int b, double* __restrict__ R,
+k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, double* __restrict__ R,
        double* __restrict__ dinv, unsigned long long* __restrict__ counters) {
   const int t = threadIdx.x;
-  const int K = nq * b;
-  // column t of A (upper part, rows 0..t) in registers
-  double a[OB_MAXB];
+  const int K = nq * B;
+  double a[B];
 #pragma unroll
-  for (int i = 0; i < OB_MAXB; ++i) a[i] = (t < b && i <= t && i < b) ? G2[(K + i) * b + t] : 0.0;
-  // reference squared norm of column t before the projections
-  const double ref = (t < b) ? ((G1 && nq > 0) ? G1[(K + t) * b + t] : G2[(K + t) * b + t]) : 0.0;
-  double rcol[OB_MAXB];  // lane t keeps column t of R
-#pragma unroll
-  for (int i = 0; i < OB_MAXB; ++i) rcol[i] = 0.0;
+  for (int i = 0; i < B; ++i) a[i] = (t < B && i <= t) ? G2[(K + i) * B + t] : 0.0;
+  const double ref = (t < B) ? ((G1 && nq > 0) ? G1[(K + t) * B + t] : G2[(K + t) * B + t]) : 0.0;
+  double rcol[B];
   int deflated = 0;
 #pragma unroll
-  for (int j = 0; j < OB_MAXB; ++j) {
-    if (j >= b) break;
-    // pivot on lane j
+  for (int j = 0; j < B; ++j) {
     const double d = __shfl_sync(0xffffffffu, a[j], j);
     const double refj = __shfl_sync(0xffffffffu, ref, j);
     const bool defl = !(d > DEFLATE_REL2 * refj) || !(d > 0.0);
@@ -261,22 +259,18 @@ k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, int
       y = y0 * (1.5 - 0.5 * d * y0 * y0);  // one Newton step: relative error ~1e-14
     }
     deflated += defl ? 1 : 0;
-    // R[j][t] = a[j] * y for t > j (lane t); R[j][j] = d * y
     const double rjt = (t > j) ? a[j] * y : ((t == j) ? d * y : 0.0);
     rcol[j] = rjt;
     if (t == j) dinv[j] = y;
-    // trailing update: a[i] -= R[j][i] * R[j][t] for j < i <= t
 #pragma unroll
-    for (int i = 0; i < OB_MAXB; ++i) {
-      if (i <= j || i >= b) continue;
+    for (int i = j + 1; i < B; ++i) {
       const double rji = __shfl_sync(0xffffffffu, rjt, i);
       if (t >= i) a[i] -= rji * rjt;
     }
   }
-  // write R (row-major, upper): lane t holds column t
 #pragma unroll
-  for (int j = 0; j < OB_MAXB; ++j)
-    if (j < b && t < b) R[j * b + t] = (j <= t) ? rcol[j] : 0.0;
+  for (int j = 0; j < B; ++j)
+    if (t < B) R[j * B + t] = (j <= t) ? rcol[j] : 0.0;
   if (t == 0 && deflated && counters) atomicAdd(&counters[2], (unsigned long long)deflated);
 }
 
@@ -341,8 +335,13 @@ k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* 
 
 int launch_chol(const double* G1, const double* G2, int nq, int b, double* R, double* dinv,
                 unsigned long long* counters, cudaStream_t st) {
-  k_chol<<<1, 32, 0, st>>>(G1, G2, nq, b, R, dinv, counters);
-  return 1;
+  switch (b) {
+    case 8: k_chol<8><<<1, 32, 0, st>>>(G1, G2, nq, R, dinv, counters); return 1;
+    case 16: k_chol<16><<<1, 32, 0, st>>>(G1, G2, nq, R, dinv, counters); return 1;
+    case 24: k_chol<24><<<1, 32, 0, st>>>(G1, G2, nq, R, dinv, counters); return 1;
+    case 32: k_chol<32><<<1, 32, 0, st>>>(G1, G2, nq, R, dinv, counters); return 1;
+    default: return 0;  // block sizes are multiples of 8 up to 32 (checked by the caller)
+  }
 }
 
 int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, double* Rout, double* P, int n, int b,
