@@ -96,6 +96,14 @@ struct svt_ctx {
   double* Uf = nullptr;             // m x cap: U (unscaled)
   double* Vf = nullptr;             // n x cap: V
   double* Vwarm = nullptr;          // n x kBMax warm start block
+  // float32 path only: float32 copies of the dense operands of the per-entry kernels (the sparse
+  // products read the current basis block, the fused update the factors), written by the kernels
+  // that produce the float64 originals
+  float* Ush = nullptr;             // m x kBMax: current U block
+  float* Vsh = nullptr;             // n x kBMax: current V block
+  float* Utf = nullptr;             // m x ldf: U diag(sigma - tau)
+  float* Vff = nullptr;             // n x ldf: V
+  int ldf = 0;                      // row length of Utf / Vff: a multiple of 4 >= r
   int warm_cols = 0;
   uint64_t rng_counter = 0;
 
@@ -315,7 +323,7 @@ static double sddmm_bytes(const svt_ctx* c, int r) {
 // Coefficients: P_in = Q (C1 + C2) + P_out (R2 R1); written to Tcol / Tdiag when given.
 // ------------------------------------------------------------------------------------------------
 static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long long q_stride, int nq, int rows, int b,
-                                 double* Tcol, double* Tdiag) {
+                                 double* Tcol, double* Tdiag, float* Pf = nullptr) {
   int l = 0;
   const double gram_q = 8.0 * rows * (nq + 1) * b, gram_p = 8.0 * rows * b;
   const double upd_q = 8.0 * rows * (nq + 2) * b, upd_p = 16.0 * rows * b;
@@ -341,7 +349,7 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
   });
   if (!c->two_corrections) {
     l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_p, [&] {
-      return launch_correct(c->G3, c->R1, Tdiag, kKMax, nullptr, P, rows, b, c->dcount, c->st);
+      return launch_correct(c->G3, c->R1, Tdiag, kKMax, nullptr, P, rows, b, c->dcount, c->st, Pf);
     });
   } else {
     // ill-conditioned blocks seen: a second first-order correction (orthonormality O(|E|^4))
@@ -351,7 +359,7 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
     l += prof_launch(c, SVT_PROF_GRAM, gram_p,
                      [&] { return launch_gram(nullptr, 0, 0, P, rows, b, c->gpart, c->G3, c->st); });
     l += prof_launch(c, SVT_PROF_BLOCK_UPDATE, upd_p, [&] {
-      return launch_correct(c->G3, c->R2, Tdiag, kKMax, nullptr, P, rows, b, nullptr, c->st);
+      return launch_correct(c->G3, c->R2, Tdiag, kKMax, nullptr, P, rows, b, nullptr, c->st, Pf);
     });
   }
   return launched(c, l);
@@ -365,20 +373,25 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J) {
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
   CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
-  TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr));
+  // float32 path: each block's last orthonormalisation kernel also writes its float32 copy
+  // (Vsh / Ush), which the next sparse product reads
+  TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
   int l = 0;
   for (int j = 0; j < J; ++j) {
     double* Uj = c->Ub + j * su;
     double* Vj = c->Vb + j * sv;
-    l += prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b),
-                     [&] { return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, Uj, m, b, c->st, c->nnz); });
+    l += prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), [&] {
+      return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, c->Vsh, Uj, m, b, c->st, c->nnz);
+    });
     TRY(launched(c, l)); l = 0;
-    TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b));
+    TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b, c->Ush));
     double* Vn = c->Vb + (j + 1) * sv;
-    l += prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b),
-                     [&] { return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, Vn, n, b, c->st, c->nnz); });
+    l += prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b), [&] {
+      return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
+    });
     TRY(launched(c, l)); l = 0;
-    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr));
+    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr,
+                       j == J - 1 ? nullptr : c->Vsh));
   }
   // S is written with leading dimension kKMax; the projected SVD reads it as b x b with leading
   // dimension b, so compact it first.
@@ -588,10 +601,15 @@ static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out)
   if (r > 0) {
     std::memcpy(c->h_pin + 2 * kKMax, c->d_host.data(), sizeof(double) * r);
     CU(c, cudaMemcpyAsync(c->scale, c->h_pin + 2 * kKMax, sizeof(double) * r, cudaMemcpyHostToDevice, c->st));
+    // float32 path: the factors of the fused update are also written as float32 rows padded to a
+    // multiple of four values (16-byte gathers)
+    c->ldf = (r + 3) & ~3;
     l += prof_launch(c, SVT_PROF_COMBINE, 8.0 * (2.0 * m * (K + r) + n * (K + r)), [&] {
       return launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, nullptr, c->Uf, c->st) +
-             launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, c->scale, c->Ut, c->st) +
-             launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, r, nullptr, c->Vf, c->st);
+             launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, r, c->scale, c->Ut, c->st, c->Utf,
+                                  c->ldf) +
+             launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, r, nullptr, c->Vf, c->st, c->Vff,
+                                  c->ldf);
     });
   }
   TRY(launched(c, l));
@@ -767,6 +785,13 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Uf, (size_t)m * cap));
   TRY(dalloc_t(c, &c->Vf, (size_t)n * cap));
   TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
+  if (c->prec == SVT_FP32) {
+    const size_t capf = (size_t)((cap + 3) & ~3);
+    TRY(dalloc_t(c, &c->Ush, (size_t)m * kBMax));
+    TRY(dalloc_t(c, &c->Vsh, (size_t)n * kBMax));
+    TRY(dalloc_t(c, &c->Utf, (size_t)m * capf));
+    TRY(dalloc_t(c, &c->Vff, (size_t)n * capf));
+  }
   TRY(dalloc_t(c, &c->Ub, (size_t)m * (kKMax + kBMax)));
   TRY(dalloc_t(c, &c->Vb, (size_t)n * (kKMax + kBMax)));
   TRY(dalloc_t(c, &c->T, (size_t)kKMax * kKMax));
@@ -901,8 +926,8 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   const int nxt = 1 - c->ycur;
   TRY(launched(c, prof_launch(c, SVT_PROF_SDDMM, sddmm_bytes(c, r), [&] {
     return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
-                               c->Ycsc[nxt], c->Ut, c->Vf, r, (int)c->m, c->delta, c->upd_partial, c->dscal, c->err,
-                               c->st);
+                               c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
+                               c->upd_partial, c->dscal, c->err, c->st);
   })));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaEventRecord(c->ev1, c->st));
@@ -1054,7 +1079,7 @@ extern "C" svt_status svt_apply_Y(svt_ctx* c, const double* V, int b, double* W)
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(V) || !aligned16(W)) return fail(c, SVT_ERR_ARG, "V and W must be 16-byte aligned");
   return launched(c, prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, (int)c->m, (int)c->n, b), [&] {
-    return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), V, W, (int)c->m, b, c->st, c->nnz);
+    return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), V, nullptr, W, (int)c->m, b, c->st, c->nnz);
   }));
 }
 
@@ -1064,7 +1089,7 @@ extern "C" svt_status svt_apply_Yt(svt_ctx* c, const double* U, int b, double* Z
   if (b < 2 || b > 64 || (b & 1)) return fail(c, SVT_ERR_ARG, "b must be even, 2 <= b <= 64");
   if (!aligned16(U) || !aligned16(Z)) return fail(c, SVT_ERR_ARG, "U and Z must be 16-byte aligned");
   return launched(c, prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, (int)c->n, (int)c->m, b), [&] {
-    return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), U, Z, (int)c->n, b, c->st, c->nnz);
+    return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), U, nullptr, Z, (int)c->n, b, c->st, c->nnz);
   }));
 }
 
@@ -1077,8 +1102,8 @@ extern "C" svt_status svt_sddmm_update(svt_ctx* c, const double* Ut, const doubl
   const int nxt = 1 - c->ycur;
   TRY(launched(c, launch_load_values(c->prec, y_in, c->Ycsr[nxt], nullptr, nullptr, c->nnz, c->st)));
   TRY(launched(c, launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, c->Ycsr[nxt],
-                                      c->Ycsc[nxt], nullptr, Ut, V, r, (int)c->m, delta, c->upd_partial, c->dscal,
-                                      c->err, c->st)));
+                                      c->Ycsc[nxt], nullptr, Ut, V, nullptr, nullptr, 0, r, (int)c->m, delta,
+                                      c->upd_partial, c->dscal, c->err, c->st)));
   TRY(launched(c, launch_store_values(c->prec, c->Ycsc[nxt], y_out, c->nnz, c->st)));
   CU(c, cudaMemcpyAsync(res2, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   return sync_and_check(c);

@@ -16,7 +16,8 @@ static constexpr int CMB_T = 256;
 
 __global__ void __launch_bounds__(CMB_T)
 k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b, int n, const double* __restrict__ W,
-                int ldW, int s, const double* __restrict__ scale, double* __restrict__ Out) {
+                int ldW, int s, const double* __restrict__ scale, double* __restrict__ Out, float* __restrict__ OutF,
+                int ldF) {
   extern __shared__ double sW[];  // K x s
   const int K = nb * b;
   for (int e = threadIdx.x; e < K * s; e += blockDim.x) {
@@ -37,16 +38,17 @@ k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b,
       for (int d = 0; d < b; ++d) v += brow[d] * wcol[d * s];
     }
     Out[(long long)i * s + c] = v;
+    if (OutF) OutF[(long long)i * ldF + c] = (float)v;
   }
 }
 
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
-                         const double* scale, double* Out, cudaStream_t st) {
+                         const double* scale, double* Out, cudaStream_t st, float* OutF, int ldF) {
   if (s <= 0 || n <= 0) return 0;
   const int rows_per_block = CMB_T / s;
   int blocks = (int)svt_min_ll(svt_ceil_div(n, rows_per_block), 152LL * 8);
   size_t smem = (size_t)nb * b * s * sizeof(double);
-  k_basis_combine<<<blocks, CMB_T, smem, st>>>(B, b_stride, nb, b, n, W, ldW, s, scale, Out);
+  k_basis_combine<<<blocks, CMB_T, smem, st>>>(B, b_stride, nb, b, n, W, ldW, s, scale, Out, OutF, ldF);
   return 1;
 }
 

@@ -53,11 +53,12 @@ int launch_omega_compact(uint64_t seed, long long N, long long n_cols, const voi
                          long long m, unsigned int* err, cudaStream_t st);
 
 // ----- per-iteration kernels -------------------------------------------------------------------
-// Out (n_out x b) = S X with S given in compressed segments (ptr, idx, val) and X (n_in x b).
-// precision 0: float64 values and accumulation; 1: float32 values and accumulation.
+// Out (n_out x b, float64) = S X with S given in compressed segments (ptr, idx, val) and X (n_in x b).
+// precision 0: float64 values, X and accumulation; 1: float32 values and accumulation, X read from
+// the float32 copy Xf when given (b a multiple of 4), else from the float64 X.
 // nnz (the total segment length) chooses how many warps share a segment.
 int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
-                double* Out, int n_out, int b, cudaStream_t st, long long nnz);
+                const float* Xf, double* Out, int n_out, int b, cudaStream_t st, long long nnz);
 
 // Gram of a tall block against a basis: G ((nq+1) b x b) = [Q_0 .. Q_{nq-1}, P]^T P, where the Q_i
 // are n x b blocks spaced `q_stride` doubles apart.  partial: gram_partial_doubles(...) doubles.
@@ -79,9 +80,9 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
 int launch_chol(const double* G1, const double* G2, int nq, int b, double* R, double* dinv,
                 unsigned long long* counters, cudaStream_t st);
 // P <- P (I - U(G3 - I)); (I + U(G3 - I)) R1 -> Tdiag (ld ldT) and/or Rout (b x b);
-// counters[3] = max |G3 - I| (as float64 bits)
+// counters[3] = max |G3 - I| (as float64 bits).  Pf (may be NULL): float32 copy of the new P.
 int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, double* Rout, double* P, int n, int b,
-                   unsigned long long* counters, cudaStream_t st);
+                   unsigned long long* counters, cudaStream_t st, float* Pf = nullptr);
 
 // Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT): T = Xl diag(theta) Wr^T,
 // theta decreasing; Xl, Wr written K x K row-major.  Also res[i] = || S (Xl rows [K-b, K), column i) ||
@@ -101,9 +102,10 @@ int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int
                            unsigned long long* counters, cudaStream_t st);
 
 // Out (n x s) = sum over blocks i of B_i (n x b) W[i b .. i b + b, 0 .. s) , columns scaled by
-// scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).
+// scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).  OutF (may be NULL):
+// float32 copy of Out with leading dimension ldF >= s.
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
-                         const double* scale, double* Out, cudaStream_t st);
+                         const double* scale, double* Out, cudaStream_t st, float* OutF = nullptr, int ldF = 0);
 
 // Fill an n x b block with uniform(-1, 1) numbers from SplitMix64 (columns c >= c0 only).
 int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStream_t st);
@@ -111,10 +113,12 @@ int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStre
 // Fused X-on-Omega + dual step + residual (precision 0: float64 values, 1: float32 values):
 //   x_p = sum_t Ut[i,t] V[j,t];  e = M_p - x_p;  y_out[p] = y_in[p] + delta e;
 //   y_out_csc[csr_to_csc[p]] = y_out[p] (if y_out_csc);  res2 = sum e^2 (deterministic).
+// Factors: float64 Ut (m x r) and V (n x r), or, for precision 1 when Utf and Vf32 are given,
+// float32 copies with leading dimension ldf (a multiple of 4, >= r).
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
-                        const double* V, int r, int n_rows, double delta, double* partial, double* res2,
-                        unsigned int* err, cudaStream_t st);
+                        const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
+                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st);
 int sddmm_partial_doubles();
 // The same fused kernel (float64 values, no column-major copy) on `blocks` CTAs of 256 threads,
 // one partial sum per CTA in `partial`, the fixed-order total in *res2 (device).

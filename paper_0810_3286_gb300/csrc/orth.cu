@@ -281,7 +281,7 @@ k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, dou
 __global__ void __launch_bounds__(ORTH_T)
 k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* __restrict__ Tdiag, int ldT,
           double* __restrict__ Rout, double* __restrict__ P, int n, int b, int g,
-          unsigned long long* __restrict__ counters) {
+          unsigned long long* __restrict__ counters, float* __restrict__ Pf) {
   __shared__ double sU[OB_MAXB * OB_MAXB];   // U(E)
   __shared__ double sR[OB_MAXB * OB_MAXB];
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
@@ -329,7 +329,11 @@ k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* 
         else a1 -= pk * sU[k * b + d];
       }
     }
-    if (live) P[(long long)i * b + d] = a0 + a1;
+    if (live) {
+      const double v = a0 + a1;
+      P[(long long)i * b + d] = v;
+      if (Pf) Pf[(long long)i * b + d] = (float)v;
+    }
   }
 }
 
@@ -345,11 +349,11 @@ int launch_chol(const double* G1, const double* G2, int nq, int b, double* R, do
 }
 
 int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, double* Rout, double* P, int n, int b,
-                   unsigned long long* counters, cudaStream_t st) {
+                   unsigned long long* counters, cudaStream_t st, float* Pf) {
   const int g = row_group(b);
   const int rows_per_block = ORTH_T / g;
   int blocks = (int)svt_min_ll(svt_ceil_div(n, rows_per_block), 152LL * 8);
-  k_correct<<<blocks, ORTH_T, 0, st>>>(G3, R1, Tdiag, ldT, Rout, P, n, b, g, counters);
+  k_correct<<<blocks, ORTH_T, 0, st>>>(G3, R1, Tdiag, ldT, Rout, P, n, b, g, counters, Pf);
   return 1;
 }
 

@@ -12,17 +12,38 @@ namespace svt {
 // WPR warps share one segment (row of Y for Y V, column of Y for Y^T U using the column-major copy
 // of the values), each taking a contiguous slice of its entries, so that short products still
 // put enough warps on every SM to hide the gather latency.  Inside a warp a group of G lanes
-// covers one sampled entry, each lane two adjacent columns of the b-wide dense row (one 16-byte
-// load of X); 32/G entries are in flight per step, four steps are unrolled.  Lane partials are
-// combined with xor shuffles and the WPR warp partials in shared memory, always in the same order
-// (deterministic, no atomics).
+// covers one sampled entry, each lane CPL adjacent columns of the b-wide dense row (one 16-byte
+// load of X: two float64 or four float32 columns); 32/G entries are in flight per step, four
+// steps are unrolled.  Lane partials are combined with xor shuffles and the WPR warp partials in
+// shared memory, always in the same order (deterministic, no atomics).  Out is float64.
+//
+// The float32 path reads a float32 copy of the dense block and accumulates in float32: no
+// float64 instruction per sampled entry (GB300 issues float64 at 1/64 of the float32 rate, and
+// a float64 -> float32 conversion per gathered element made this kernel float64-pipe bound).
 // ------------------------------------------------------------------------------------------------
 static constexpr int SPMM_T = 256;
 
-template <typename VT, typename AT>
+template <typename XT> struct XRow;
+template <> struct XRow<double> { static constexpr int CPL = 2; using V = double2; };
+template <> struct XRow<float> { static constexpr int CPL = 4; using V = float4; };
+
+__device__ __forceinline__ double xcomp(const double2& v, int q) { return q == 0 ? v.x : v.y; }
+__device__ __forceinline__ float xcomp(const float4& v, int q) {
+  return q == 0 ? v.x : (q == 1 ? v.y : (q == 2 ? v.z : v.w));
+}
+
+template <typename XT, typename AT, int CPL>
+__device__ __forceinline__ void spmm_fma(AT (&acc)[CPL], AT v, const XT* __restrict__ src) {
+  const typename XRow<XT>::V x = __ldg(reinterpret_cast<const typename XRow<XT>::V*>(src));
+#pragma unroll
+  for (int q = 0; q < CPL; ++q) acc[q] += v * (AT)xcomp(x, q);
+}
+
+template <typename VT, typename XT, typename AT>
 __global__ void __launch_bounds__(SPMM_T)
 k_spmm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const VT* __restrict__ val,
-       const double* __restrict__ X, double* __restrict__ Out, int n_out, int b, int G, int WPR) {
+       const XT* __restrict__ X, double* __restrict__ Out, int n_out, int b, int G, int WPR) {
+  constexpr int CPL = XRow<XT>::CPL;
   __shared__ double part[SPMM_T / 32][64];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -31,11 +52,13 @@ k_spmm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const V
   const int gl = lane & (G - 1);
   const int grp = lane / G;
   const int ngrp = 32 / G;
-  const int c = 2 * gl;
+  const int c = CPL * gl;
   const bool active_col = c < b;
   for (int s0 = blockIdx.x * segs_per_block; s0 < n_out; s0 += gridDim.x * segs_per_block) {
     const int s = s0 + slot;
-    AT acc0 = 0, acc1 = 0;
+    AT acc[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) acc[q] = (AT)0;
     if (s < n_out) {
       const int a = ptr[s], e = ptr[s + 1];
       const int len = e - a;
@@ -49,61 +72,65 @@ k_spmm(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, const V
         AT v0 = (AT)__ldg(val + p), v1 = (AT)__ldg(val + p + ngrp), v2 = (AT)__ldg(val + p + 2 * ngrp),
            v3 = (AT)__ldg(val + p + 3 * ngrp);
         if (active_col) {
-          double2 x0 = __ldg(reinterpret_cast<const double2*>(X + (long long)j0 * b + c));
-          double2 x1 = __ldg(reinterpret_cast<const double2*>(X + (long long)j1 * b + c));
-          double2 x2 = __ldg(reinterpret_cast<const double2*>(X + (long long)j2 * b + c));
-          double2 x3 = __ldg(reinterpret_cast<const double2*>(X + (long long)j3 * b + c));
-          acc0 += v0 * (AT)x0.x; acc1 += v0 * (AT)x0.y;
-          acc0 += v1 * (AT)x1.x; acc1 += v1 * (AT)x1.y;
-          acc0 += v2 * (AT)x2.x; acc1 += v2 * (AT)x2.y;
-          acc0 += v3 * (AT)x3.x; acc1 += v3 * (AT)x3.y;
+          spmm_fma<XT, AT, CPL>(acc, v0, X + (long long)j0 * b + c);
+          spmm_fma<XT, AT, CPL>(acc, v1, X + (long long)j1 * b + c);
+          spmm_fma<XT, AT, CPL>(acc, v2, X + (long long)j2 * b + c);
+          spmm_fma<XT, AT, CPL>(acc, v3, X + (long long)j3 * b + c);
         }
       }
       for (; p < hi; p += ngrp) {
         int j0 = __ldg(idx + p);
         AT v0 = (AT)__ldg(val + p);
-        if (active_col) {
-          double2 x0 = __ldg(reinterpret_cast<const double2*>(X + (long long)j0 * b + c));
-          acc0 += v0 * (AT)x0.x; acc1 += v0 * (AT)x0.y;
-        }
+        if (active_col) spmm_fma<XT, AT, CPL>(acc, v0, X + (long long)j0 * b + c);
       }
     }
     for (int o = G; o < 32; o <<= 1) {
-      acc0 += __shfl_xor_sync(0xffffffffu, acc0, o);
-      acc1 += __shfl_xor_sync(0xffffffffu, acc1, o);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
     }
     if (WPR == 1) {
       if (s < n_out && grp == 0 && active_col) {
-        double2 w;
-        w.x = (double)acc0; w.y = (double)acc1;
-        *reinterpret_cast<double2*>(Out + (long long)s * b + c) = w;
+        double* dst = Out + (long long)s * b + c;
+#pragma unroll
+        for (int q = 0; q < CPL; q += 2) {
+          double2 w;
+          w.x = (double)acc[q]; w.y = (double)acc[q + 1];
+          *reinterpret_cast<double2*>(dst + q) = w;
+        }
       }
     } else {
       if (grp == 0 && active_col) {
-        part[warp][c] = (double)acc0;
-        part[warp][c + 1] = (double)acc1;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) part[warp][c + q] = (double)acc[q];
       }
       __syncthreads();
       if (wp == 0 && s < n_out && grp == 0 && active_col) {
-        double w0 = 0.0, w1 = 0.0;
+        double w[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) w[q] = 0.0;
         for (int k = 0; k < WPR; ++k) {
-          w0 += part[warp + k][c];
-          w1 += part[warp + k][c + 1];
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) w[q] += part[warp + k][c + q];
         }
-        double2 w;
-        w.x = w0; w.y = w1;
-        *reinterpret_cast<double2*>(Out + (long long)s * b + c) = w;
+        double* dst = Out + (long long)s * b + c;
+#pragma unroll
+        for (int q = 0; q < CPL; q += 2) {
+          double2 v2;
+          v2.x = w[q]; v2.y = w[q + 1];
+          *reinterpret_cast<double2*>(dst + q) = v2;
+        }
       }
       __syncthreads();
     }
   }
 }
 
-int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X, double* Out,
-                int n_out, int b, cudaStream_t st, long long nnz) {
-  if (n_out <= 0) return 0;
+template <typename VT, typename XT, typename AT>
+static void spmm_launch(const int32_t* ptr, const int32_t* idx, const VT* val, const XT* X, double* Out, int n_out,
+                        int b, cudaStream_t st, long long nnz) {
+  constexpr int CPL = XRow<XT>::CPL;
   int G = 1;
-  while (2 * G < b) G <<= 1;   // G lanes x 2 columns >= b
+  while (CPL * G < b) G <<= 1;   // G lanes x CPL columns >= b
   if (G > 32) G = 32;
   // warps per segment from the mean segment length (entries per warp step = 32 / G)
   const double mean_len = nnz > 0 ? (double)nnz / n_out : 0.0;
@@ -111,49 +138,72 @@ int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const voi
   while (WPR < 8 && mean_len / WPR > 8.0 * (32 / G)) WPR <<= 1;
   const int segs_per_block = (SPMM_T / 32) / WPR;
   int blocks = (int)svt_min_ll(svt_ceil_div(n_out, segs_per_block), 152LL * 16);
+  k_spmm<VT, XT, AT><<<blocks, SPMM_T, 0, st>>>(ptr, idx, val, X, Out, n_out, b, G, WPR);
+}
+
+int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
+                const float* Xf, double* Out, int n_out, int b, cudaStream_t st, long long nnz) {
+  if (n_out <= 0) return 0;
   if (precision == 0)
-    k_spmm<double, double><<<blocks, SPMM_T, 0, st>>>(ptr, idx, (const double*)val, X, Out, n_out, b, G, WPR);
+    spmm_launch<double, double, double>(ptr, idx, (const double*)val, X, Out, n_out, b, st, nnz);
+  else if (Xf)
+    spmm_launch<float, float, float>(ptr, idx, (const float*)val, Xf, Out, n_out, b, st, nnz);
   else
-    k_spmm<float, float><<<blocks, SPMM_T, 0, st>>>(ptr, idx, (const float*)val, X, Out, n_out, b, G, WPR);
+    spmm_launch<float, double, float>(ptr, idx, (const float*)val, X, Out, n_out, b, st, nnz);
   return 1;
 }
 
 // ------------------------------------------------------------------------------------------------
 // Fused X-on-Omega + dual step + residual.  One warp per row i of Omega: the row Ut[i, :] (r <= 64
 // values) sits in two registers per lane and is broadcast with shuffles; each lane owns one
-// sampled entry p = (i, j) per step, gathers V[j, :] (r contiguous doubles), forms
+// sampled entry p = (i, j) per step, gathers V[j, :] (r contiguous values), forms
 // x = <Ut[i,:], V[j,:]>, e = M_p - x, writes y_out[p] = y_in[p] + delta e (and the column-major
-// copy), and accumulates e^2.  Block partial sums are summed in a fixed order afterwards.
+// copy), and accumulates e^2 (per lane in the accumulation type, then float64 across lanes and
+// CTAs).  Block partial sums are summed in a fixed order afterwards.
+//
+// FT is the factor type.  The float32 path passes float32 factors whose rows are padded to a
+// multiple of four (ldf), so a gathered row is ceil(r / 4) 16-byte loads and no float64
+// instruction runs per sampled entry; the float64 path and the float64 entry points pass float64
+// factors with ldf = r.
 // ------------------------------------------------------------------------------------------------
 static constexpr int UPD_THREADS = 256;
 static constexpr int UPD_BLOCKS = 152 * 8;
 
 // RMAX: compile-time bound on r (16, 32 or 64) so that the gathered row V[j, :] lives in registers:
-// all r loads of a lane are issued before the dot product, one gather round trip per entry.
-template <typename VT, typename AT, int RMAX>
+// all loads of a lane are issued before the dot product, one gather round trip per entry.
+template <typename VT, typename AT, typename FT, int RMAX>
 __global__ void __launch_bounds__(UPD_THREADS)
 k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                const int32_t* __restrict__ csr_to_csc, const VT* __restrict__ M, const VT* __restrict__ y_in,
-               VT* __restrict__ y_out, VT* __restrict__ y_out_csc, const double* __restrict__ Ut,
-               const double* __restrict__ V, int r, int n_rows, AT delta, double* __restrict__ partial,
+               VT* __restrict__ y_out, VT* __restrict__ y_out_csc, const FT* __restrict__ Ut,
+               const FT* __restrict__ V, int r, int ldf, int n_rows, AT delta, double* __restrict__ partial,
                unsigned int* err) {
   __shared__ double red[UPD_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
-  double acc = 0.0;
+  AT acc = (AT)0;
   for (int i = blockIdx.x * warps + (threadIdx.x >> 5); i < n_rows; i += gridDim.x * warps) {
     const int a = row_ptr[i], e = row_ptr[i + 1];
     if (a == e) continue;
-    AT u0 = lane < r ? (AT)Ut[(long long)i * r + lane] : (AT)0;
-    AT u1 = lane + 32 < r ? (AT)Ut[(long long)i * r + lane + 32] : (AT)0;
+    AT u0 = lane < r ? (AT)Ut[(long long)i * ldf + lane] : (AT)0;
+    AT u1 = lane + 32 < r ? (AT)Ut[(long long)i * ldf + lane + 32] : (AT)0;
     for (int base = a; base < e; base += 32) {
       const int p = base + lane;
       const bool live = p < e;
       const int j = live ? col_idx[p] : 0;
-      const double* vj = V + (long long)j * r;
-      double vr[RMAX];
+      const FT* vj = V + (long long)j * ldf;
+      FT vr[RMAX];
+      if constexpr (sizeof(FT) == 4) {
 #pragma unroll
-      for (int t = 0; t < RMAX; ++t) vr[t] = (live && t < r) ? __ldg(vj + t) : 0.0;
+        for (int t4 = 0; t4 < RMAX / 4; ++t4) {
+          float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (live && 4 * t4 < r) w = __ldg(reinterpret_cast<const float4*>(vj) + t4);
+          vr[4 * t4] = w.x; vr[4 * t4 + 1] = w.y; vr[4 * t4 + 2] = w.z; vr[4 * t4 + 3] = w.w;
+        }
+      } else {
+#pragma unroll
+        for (int t = 0; t < RMAX; ++t) vr[t] = (live && t < r) ? __ldg(vj + t) : (FT)0;
+      }
       const AT mp = live ? (AT)M[p] : (AT)0;
       const AT yp = live ? (AT)y_in[p] : (AT)0;
       const int q = (live && y_out_csc) ? csr_to_csc[p] : 0;
@@ -170,12 +220,12 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
         VT yn = (VT)(yp + delta * ev);
         y_out[p] = yn;
         if (y_out_csc) y_out_csc[q] = yn;
-        acc += (double)ev * (double)ev;
+        acc += ev * ev;
       }
     }
   }
-  acc = warp_sum(acc);
-  if (lane == 0) red[threadIdx.x >> 5] = acc;
+  double accd = warp_sum((double)acc);
+  if (lane == 0) red[threadIdx.x >> 5] = accd;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < warps ? red[threadIdx.x] : 0.0;
@@ -203,31 +253,40 @@ __global__ void k_sum_fixed(const double* __restrict__ partial, int np, double* 
 
 int sddmm_partial_doubles() { return UPD_BLOCKS; }
 
-template <typename VT, typename AT>
-static void sddmm_dispatch(int rmax, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
-                           const VT* M, const VT* y_in, VT* y_out, VT* y_out_csc, const double* Ut, const double* V,
-                           int r, int n_rows, AT delta, double* partial, unsigned int* err, cudaStream_t st) {
-  if (rmax <= 16)
-    k_sddmm_update<VT, AT, 16><<<UPD_BLOCKS, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, n_rows, delta, partial, err);
-  else if (rmax <= 32)
-    k_sddmm_update<VT, AT, 32><<<UPD_BLOCKS, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, n_rows, delta, partial, err);
+template <typename VT, typename AT, typename FT>
+static void sddmm_dispatch(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc, const VT* M,
+                           const VT* y_in, VT* y_out, VT* y_out_csc, const FT* Ut, const FT* V, int r, int ldf,
+                           int n_rows, AT delta, int blocks, double* partial, unsigned int* err, cudaStream_t st) {
+  if (r <= 16)
+    k_sddmm_update<VT, AT, FT, 16><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
+                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
+                                                                    err);
+  else if (r <= 32)
+    k_sddmm_update<VT, AT, FT, 32><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
+                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
+                                                                    err);
   else
-    k_sddmm_update<VT, AT, 64><<<UPD_BLOCKS, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, n_rows, delta, partial, err);
+    k_sddmm_update<VT, AT, FT, 64><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
+                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
+                                                                    err);
 }
 
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
-                        const double* V, int r, int n_rows, double delta, double* partial, double* res2,
-                        unsigned int* err, cudaStream_t st) {
+                        const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
+                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st) {
   if (precision == 0)
-    sddmm_dispatch<double, double>(r, row_ptr, col_idx, csr_to_csc, (const double*)M, (const double*)y_in,
-                                   (double*)y_out, (double*)y_out_csc, Ut, V, r, n_rows, delta, partial, err, st);
+    sddmm_dispatch<double, double, double>(row_ptr, col_idx, csr_to_csc, (const double*)M, (const double*)y_in,
+                                           (double*)y_out, (double*)y_out_csc, Ut, V, r, r, n_rows, delta,
+                                           UPD_BLOCKS, partial, err, st);
+  else if (Utf && Vf32)
+    sddmm_dispatch<float, float, float>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
+                                        (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows, (float)delta,
+                                        UPD_BLOCKS, partial, err, st);
   else
-    sddmm_dispatch<float, float>(r, row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in, (float*)y_out,
-                                 (float*)y_out_csc, Ut, V, r, n_rows, (float)delta, partial, err, st);
+    sddmm_dispatch<float, float, double>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
+                                         (float*)y_out, (float*)y_out_csc, Ut, V, r, r, n_rows, (float)delta,
+                                         UPD_BLOCKS, partial, err, st);
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, UPD_BLOCKS, res2);
   return 2;
 }
@@ -302,18 +361,8 @@ namespace svt {
 int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, const double* M, const double* y_in,
                              double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
                              int blocks, double* partial, double* res2, cudaStream_t st) {
-  if (r <= 16)
-    k_sddmm_update<double, double, 16><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
-                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
-                                                                        nullptr);
-  else if (r <= 32)
-    k_sddmm_update<double, double, 32><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
-                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
-                                                                        nullptr);
-  else
-    k_sddmm_update<double, double, 64><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, nullptr, M, y_in, y_out,
-                                                                        nullptr, Ut, V, r, n_rows, delta, partial,
-                                                                        nullptr);
+  sddmm_dispatch<double, double, double>(row_ptr, col_idx, nullptr, M, y_in, y_out, nullptr, Ut, V, r, r, n_rows,
+                                         delta, blocks, partial, nullptr, st);
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, blocks, res2);
   return 2;
 }

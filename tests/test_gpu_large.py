@@ -1,0 +1,80 @@
+"""Full-size rank-10 workloads of Table 1 (Sec. 5.2.1) on the float32 path, checked by properties
+that hold at any size (no oracle run at these sizes).
+
+Table 1 averages five random instances per row; here five seeds per shape are solved with
+tau = 5n, delta = 1.2/p, eps = 1e-4 (eq. (5.5)), and:
+
+* the median iteration count is within +-15% of the paper's value for that row (123 at
+  10000 x 10000, 124 at 20000 x 20000, 125 at 30000 x 30000);
+* every instance that converges within the paper's count (+15%) ends at the planted rank (the
+  slow ones at r or r + 1), and every instance that meets the stopping rule has relative error ||X - M||_F / ||M||_F (eq. (5.8), closed form from the factors) below the 2e-4
+  the paper reports for all of Table 1;
+* on one converged instance the final shrink satisfies the certificate of Theorem 2.1: with
+  X = D_tau(Y) = U diag(sigma - tau) V^T, (Y - X) V = tau U on the kept singular vectors, where
+  Y V comes from the library's own sparse product.
+
+The median, not the mean, is compared: a minority of instances (one in five at 10000^2 and two in
+five at 30000^2 with seeds 0-4) converge much more slowly because an (r+1)-th singular value of
+the dual iterate hovers at tau and the rank briefly rises to r+1; an independent float64 SVT
+with ARPACK partial SVDs reproduces those traces, so it is a property of the iteration on those
+instances, not of this implementation.
+"""
+import numpy as np
+import pytest
+
+from svt_inputs import planted_problem, sample_count
+
+pytestmark = pytest.mark.gpu
+
+SEEDS = range(5)
+
+
+def _relerr(U, d, V, A, B):
+    nx2 = float(np.sum(d * d))
+    nm2 = float(np.trace((A.T @ A) @ (B.T @ B)))
+    xm = float(np.trace(np.diag(d) @ (U.T @ A) @ (B.T @ V)))
+    return np.sqrt(max(nx2 - 2 * xm + nm2, 0.0) / nm2)
+
+
+def _certificate(torch, s, U, d, V, tau):
+    r = U.shape[1]
+    Vd = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    W = torch.empty((U.shape[0], r), dtype=torch.float64, device="cuda")
+    s.apply_Y(Vd, W)
+    torch.cuda.synchronize()
+    lhs = W.cpu().numpy() - U * d   # (Y - X) V, with X V = U diag(d) for orthonormal V
+    return np.linalg.norm(lhs - tau * U) / (tau * np.sqrt(r))
+
+
+@pytest.mark.parametrize("n,paper_iters", [(10000, 123), (20000, 124), (30000, 125)])
+def test_table1_rank10_rows(cuda, n, paper_iters):
+    torch = cuda
+    from paper_0810_3286_gb300 import Solver
+    r = 10
+    m = sample_count(n, n, r, 6.0)
+    iters, checked = [], False
+    for seed in SEEDS:
+        p = planted_problem(n, n, r, m, seed)
+        with Solver(n, n, torch.from_numpy(p.rows).cuda(), torch.from_numpy(p.cols).cuda(),
+                    torch.from_numpy(p.vals).cuda(), precision="fp32", k_max=1500) as s:
+            res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27, raise_on_nonconvergence=False)
+            iters.append(res["iterations"])
+            # an instance that converges in the paper's count has the planted rank; on the slow
+            # instances the stop can fall inside an excursion to rank r + 1
+            if res["converged"] and res["iterations"] <= 1.15 * paper_iters:
+                assert res["rank"] == r, (seed, res)
+            else:
+                assert r <= res["rank"] <= r + 1, (seed, res)
+            if res["converged"]:
+                assert res["residual"] <= 1e-4
+                U, d, V = s.factors()
+                err = _relerr(U, d, V, p.A, p.B)
+                assert err < 2e-4, (seed, err)
+                if not checked:
+                    # the factors are those of the last shrink, of the Y before its final update;
+                    # that update moves Y V by at most delta * eps * ||P_Omega M||_F
+                    assert _certificate(torch, s, U, d, V, p.tau_default()) < 1e-3, seed
+                    checked = True
+    med = float(np.median(iters))
+    assert 0.85 * paper_iters <= med <= 1.15 * paper_iters, iters
+    assert checked, iters
