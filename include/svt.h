@@ -60,7 +60,8 @@ enum { SVT_FP64 = 0, SVT_FP32 = 1 };
 
 typedef struct svt_options {
   int precision;          /* SVT_FP64 (default) or SVT_FP32 */
-  int block;              /* Lanczos block size b (multiple of 8, <= 32); 0 = automatic */
+  int block;              /* lower bound on the Lanczos block size b (rounded up to a multiple of 8,
+                             at most 32); 0 = automatic: wanted triplets + max(4, wanted / 4) */
   int ell;                /* rank increment l of Sec. 5.1.1 (default 5) */
   int k_max;              /* maximum SVT iterations after the kick (default 1000) */
   int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J*b <= 96) */
@@ -72,6 +73,9 @@ typedef struct svt_options {
   void* stream;           /* cudaStream_t the caller orders work on; NULL = default stream.  The
                              library works on a stream of its own and joins it to this stream with
                              events at the start and end of every call. */
+  int fused_orth;         /* 1 (default): each block orthonormalisation runs as one cooperative
+                             kernel with grid barriers where the device supports cooperative
+                             launches; 0: as a sequence of eight kernels (same arithmetic) */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
@@ -247,14 +251,16 @@ int64_t svt_kernel_launches(const svt_ctx* ctx);
  *   SVT_PROF_SPMM (Y V), SVT_PROF_SPMM_T (Y^T U), SVT_PROF_GRAM (basis Gram products),
  *   SVT_PROF_BLOCK_UPDATE (P <- (P - Q C) R^-1), SVT_PROF_SMALL (b x b Cholesky steps),
  *   SVT_PROF_JACOBI (projected SVD), SVT_PROF_COMBINE (Ritz vectors), SVT_PROF_SDDMM (fused X on
- *   Omega + dual step).
+ *   Omega + dual step), SVT_PROF_ORTH (a whole block orthonormalisation in one cooperative kernel,
+ *   which replaces the GRAM / BLOCK_UPDATE / SMALL launches of that block where the device
+ *   supports cooperative launches).
  * svt_set_profile selects the classes whose launches are bracketed by CUDA events on the context
  * stream (0 = none) and clears the totals.  svt_get_profile writes, per class, the number of
  * bracketed launch groups, their total device time in milliseconds and the algorithmic bytes they
  * move (arrays of SVT_PROF_CLASSES entries; any pointer may be NULL).  Both synchronise the stream.
  */
 enum { SVT_PROF_SPMM = 0, SVT_PROF_SPMM_T, SVT_PROF_GRAM, SVT_PROF_BLOCK_UPDATE, SVT_PROF_SMALL, SVT_PROF_JACOBI,
-       SVT_PROF_COMBINE, SVT_PROF_SDDMM, SVT_PROF_CLASSES };
+       SVT_PROF_COMBINE, SVT_PROF_SDDMM, SVT_PROF_ORTH, SVT_PROF_CLASSES };
 svt_status svt_set_profile(svt_ctx* ctx, unsigned int class_mask);
 svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes);
 

@@ -70,7 +70,7 @@ class Solver:
 
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
-                 max_cycles: int = 40, use_graphs: bool = True):
+                 max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -82,6 +82,8 @@ class Solver:
         opt.seed = seed
         opt.max_cycles = max_cycles
         opt.use_graphs = 1 if use_graphs else 0
+        opt.fused_orth = 1 if fused_orth else 0
+        opt.block = int(block)
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda

@@ -47,6 +47,7 @@ class svt_options(ctypes.Structure):
         ("use_graphs", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("stream", ctypes.c_void_p),
+        ("fused_orth", ctypes.c_int),
     ]
 
 
@@ -122,7 +123,7 @@ COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "
                  "max_orth_defect", "kernel_launches", "reserved"]
 
 # kernel classes of svt_set_profile / svt_get_profile
-PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update"]
+PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update", "orth"]
 
 _lock = threading.Lock()
 _lib = None

@@ -113,6 +113,8 @@ struct svt_ctx {
   double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
   double *Rkeep = nullptr, *scale = nullptr;
   bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
+  int coop_grid = 0;                      // > 0: orthonormalise each block in one cooperative kernel
+  void* gbar = nullptr;                   // its grid barrier (8 bytes, zeroed)
   double* R2 = nullptr;                   // b x b product of the first correction and R1
   unsigned long long* dcount = nullptr;   // device counters: [0] Jacobi calls [1] Jacobi sweeps
                                           // [2] deflated columns [3] max orthonormality defect (bits)
@@ -258,6 +260,11 @@ static svt_status sync_and_check(svt_ctx* c) {
     if (e & SVT_DEVERR_NONFINITE) return fail(c, SVT_ERR_NUMERIC, "NaN or Inf in the residual");
     if (e & SVT_DEVERR_CAPACITY) return fail(c, SVT_ERR_INTERNAL, "device buffer capacity exceeded");
     if (e & SVT_DEVERR_JACOBI) return fail(c, SVT_ERR_NUMERIC, "projected Jacobi SVD did not converge");
+    if (e & SVT_DEVERR_BARRIER) {
+      // a cooperative kernel gave up at a grid barrier: reset it for later launches
+      if (c->gbar) CU(c, cudaMemsetAsync(c->gbar, 0, 8, c->st));
+      return fail(c, SVT_ERR_TIMEOUT, "a grid barrier of the cooperative orthonormalisation timed out");
+    }
     // SVT_DEVERR_CHOL is informational (deflation handled in-kernel)
   }
   return SVT_OK;
@@ -288,8 +295,11 @@ static svt_status d2h_sync(svt_ctx* c, void* dst, const void* src, size_t bytes)
   return SVT_OK;
 }
 
-static int choose_block(int s_need) {
+// Block size for s_need wanted triplets: s_need plus max(4, s_need / 4) spare columns, at least the
+// block option, rounded up to a multiple of 8, at most kBMax.
+static int choose_block(const svt_ctx* c, int s_need) {
   int b = s_need + std::max(kOversample, s_need / 4);
+  if (c->opt.block > b) b = c->opt.block;
   b = (b + 7) / 8 * 8;
   if (b > kBMax) b = kBMax;
   if (b < 8) b = 8;
@@ -325,6 +335,18 @@ static double sddmm_bytes(const svt_ctx* c, int r) {
 static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long long q_stride, int nq, int rows, int b,
                                  double* Tcol, double* Tdiag, float* Pf = nullptr) {
   int l = 0;
+  if (c->coop_grid > 0) {
+    // one cooperative kernel: gram / update / Cholesky / update / correction phases with grid
+    // barriers (same arithmetic as the launch sequence below)
+    const double bytes = 8.0 * rows * b * (3.0 * (nq + 1) + 2.0 * nq + 3.0);
+    l += prof_launch(c, SVT_PROF_ORTH, bytes, [&] {
+      return launch_orth_coop(P, Q, q_stride, nq, rows, b, c->gpart, c->G1, c->G2, c->G3, Tcol, Tdiag, kKMax, Pf,
+                              c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st);
+    });
+    if (l == 0) return fail(c, SVT_ERR_CUDA, "cooperative orthonormalisation launch failed: %s",
+                            cudaGetErrorString(cudaGetLastError()));
+    return launched(c, l);
+  }
   const double gram_q = 8.0 * rows * (nq + 1) * b, gram_p = 8.0 * rows * b;
   const double upd_q = 8.0 * rows * (nq + 2) * b, upd_p = 16.0 * rows * b;
   const double* G1 = nullptr;
@@ -525,7 +547,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-10 : 1e-6);
   int s = std::min(s_init, kmin);
   int passes = 1;
-  int b = choose_block(s);
+  int b = choose_block(c, s);
   int J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
   c->last_cycles = 0;
   c->last_spmm = 0;
@@ -560,7 +582,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
         }
         s = std::min(s + c->opt.ell, kmin);
         ++passes;
-        int nb = choose_block(s);
+        int nb = choose_block(c, s);
         TRY(keep_ritz(c, b, J, std::min(b, nb)));
         b = nb;
         J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
@@ -634,8 +656,10 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->max_cycles = 40;
   opt->lanczos_tol = 0.0;
   opt->indices_on_device = 0;
+  opt->use_graphs = 1;
   opt->seed = 0x5eed5eedULL;
   opt->stream = nullptr;
+  opt->fused_orth = 1;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -807,6 +831,8 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->R2, kBMax * kBMax));
   TRY(dalloc_t(c, &c->dinv, kBMax));
   TRY(dalloc_t(c, &c->dcount, 8));
+  TRY(dalloc(c, &c->gbar, 8));
+  CU(c, cudaMemsetAsync(c->gbar, 0, 8, c->st));
   CU(c, cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->st));
   // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
   TRY(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
@@ -871,6 +897,8 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   } else if (init_jacobi_attributes() != 0) {
     s = fail(c, SVT_ERR_CUDA, "setting the shared-memory limit of the projected-SVD kernels failed");
   } else {
+    // the partial-Gram buffer holds at most 2 * 152 row chunks (gram_partial_doubles)
+    c->coop_grid = o.fused_orth ? std::min(orth_coop_init(), 2 * 152) : 0;
     s = create_body(c, rows, cols, M_omega);
   }
   if (s != SVT_OK) {

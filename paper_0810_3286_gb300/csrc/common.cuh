@@ -13,6 +13,7 @@ enum : unsigned int {
   SVT_DEVERR_CHOL = 1u << 3,          // a Gram matrix was not numerically positive definite
   SVT_DEVERR_CAPACITY = 1u << 4,      // a device buffer would have overflowed (write skipped)
   SVT_DEVERR_JACOBI = 1u << 5,        // the small Jacobi SVD hit its sweep limit
+  SVT_DEVERR_BARRIER = 1u << 6,       // a grid barrier of a cooperative kernel gave up waiting
 };
 
 __device__ __forceinline__ void svt_set_error(unsigned int* err, unsigned int bit) {
@@ -29,6 +30,40 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Grid-wide barrier of a cooperative launch (all CTAs co-resident), on one 32-bit word: CTA 0 adds
+// 2^31 - (nb - 1) and every other CTA adds 1, so one complete barrier changes the word by exactly
+// 2^31 and flips its top bit once, while no partial sum of the arrivals reaches it; a CTA waits
+// until the top bit differs from the one it saw on arrival.  One atomic per CTA, no reset between
+// barriers or launches.  The wait is bounded: after kBarrierSpinLimit polls (far beyond any
+// legitimate wait) the CTA records SVT_DEVERR_BARRIER and the call returns false; the caller then
+// returns from the kernel, and the host zeroes the word before the next launch.
+static constexpr unsigned int kBarrierSpinLimit = 1u << 22;
+
+__device__ __forceinline__ bool svt_grid_barrier(unsigned int* word, unsigned int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int inc = (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) ? 0x80000000u - (nb - 1u) : 1u;
+    __threadfence();
+    const unsigned int old = atomicAdd(word, inc);
+    volatile unsigned int* vw = word;
+    unsigned int it = 0;
+    while (((*vw ^ old) & 0x80000000u) == 0u) {
+      if (++it > kBarrierSpinLimit) {
+        ok = 0;
+        svt_set_error(err, SVT_DEVERR_BARRIER);
+        break;
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 static inline int svt_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -17,6 +17,8 @@
 //                                       O(|E|^4))
 // The coefficients satisfy P_in = Q (C1 + C2) + P_out R2 R1 exactly for the factors used; C1 + C2
 // and R2 R1 are the entries of the projected block bidiagonal matrix.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -162,22 +164,12 @@ int launch_gram(const double* Q, long long q_stride, int nq, const double* P, in
 //   mode 0: P <- P - Q C,             partial of [Q, P]^T P   (second projection pass follows)
 //   mode 1: P <- (P - Q C) R^-1,      partial of P^T P        (correction pass follows)
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(ORTH_T)
-k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ C,
-              const double* __restrict__ R, const double* __restrict__ dinv, double* __restrict__ P, int n, int b,
-              int g, int rows_per_cta, double* __restrict__ partial) {
-  __shared__ double sC[OB_MAXK * OB_MAXB];
-  __shared__ double sR[OB_MAXB * OB_MAXB];
-  __shared__ double sD[OB_MAXB];
-  const int K = nq * b;
-  for (int t = threadIdx.x; t < K * b; t += blockDim.x) sC[t] = C[t];
-  if (mode == 1) {
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) sR[t] = R[t];
-    for (int t = threadIdx.x; t < b; t += blockDim.x) sD[t] = dinv[t];
-  }
-  __syncthreads();
-  const int r0 = blockIdx.x * rows_per_cta;
-  const int r1 = min(n, r0 + rows_per_cta);
+// Rows [r0, r1) of P, g lanes per row (lane d owns column d < b):
+//   mode 0: P <- P - Q C;   mode 1: P <- (P - Q C) R^-1 with dinv = 1 / diag(R)
+// C (nq b x b), R (b x b) and dinv (b) in shared memory.  Called by all threads of the CTA.
+__device__ void update_rows(int mode, const double* __restrict__ Q, long long q_stride, int nq,
+                            const double* __restrict__ sC, const double* __restrict__ sR,
+                            const double* __restrict__ sD, double* __restrict__ P, int b, int g, int r0, int r1) {
   const int rows_per_iter = ORTH_T / g;
   const int rl = threadIdx.x / g, d = threadIdx.x - rl * g;
   const int gbase = (threadIdx.x & 31) & ~(g - 1);
@@ -214,6 +206,25 @@ k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq
     }
     if (live) P[(long long)i * b + d] = v;
   }
+}
+
+__global__ void __launch_bounds__(ORTH_T)
+k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ C,
+              const double* __restrict__ R, const double* __restrict__ dinv, double* __restrict__ P, int n, int b,
+              int g, int rows_per_cta, double* __restrict__ partial) {
+  __shared__ double sC[OB_MAXK * OB_MAXB];
+  __shared__ double sR[OB_MAXB * OB_MAXB];
+  __shared__ double sD[OB_MAXB];
+  const int K = nq * b;
+  for (int t = threadIdx.x; t < K * b; t += blockDim.x) sC[t] = C[t];
+  if (mode == 1) {
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) sR[t] = R[t];
+    for (int t = threadIdx.x; t < b; t += blockDim.x) sD[t] = dinv[t];
+  }
+  __syncthreads();
+  const int r0 = blockIdx.x * rows_per_cta;
+  const int r1 = min(n, r0 + rows_per_cta);
+  update_rows(mode, Q, q_stride, nq, sC, sR, sD, P, b, g, r0, r1);
   __syncthreads();
   gram_chunk(Q, q_stride, mode == 0 ? nq : 0, P, b, r0, r1, partial);
 }
@@ -236,16 +247,18 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
 // by one float64 Newton step (relative error ~1e-14; the float32 seed alone would leave errors of
 // 1e-7 times the condition number of the Gram, which reaches 1e3 - 1e4 in Krylov blocks).
 // ------------------------------------------------------------------------------------------------
+// One warp (lanes 0..31 of the calling warp).  G1 / G2 may have been written by other CTAs of the
+// same kernel: they are read through L2.
 template <int B>
-__global__ void __launch_bounds__(32)
-k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, double* __restrict__ R,
-       double* __restrict__ dinv, unsigned long long* __restrict__ counters) {
-  const int t = threadIdx.x;
+__device__ __forceinline__ void chol_warp(const double* __restrict__ G1, const double* __restrict__ G2, int nq,
+                                          double* __restrict__ R, double* __restrict__ dinv,
+                                          unsigned long long* __restrict__ counters) {
+  const int t = threadIdx.x & 31;
   const int K = nq * B;
   double a[B];
 #pragma unroll
-  for (int i = 0; i < B; ++i) a[i] = (t < B && i <= t) ? G2[(K + i) * B + t] : 0.0;
-  const double ref = (t < B) ? ((G1 && nq > 0) ? G1[(K + t) * B + t] : G2[(K + t) * B + t]) : 0.0;
+  for (int i = 0; i < B; ++i) a[i] = (t < B && i <= t) ? __ldcg(G2 + (K + i) * B + t) : 0.0;
+  const double ref = (t < B) ? ((G1 && nq > 0) ? __ldcg(G1 + (K + t) * B + t) : __ldcg(G2 + (K + t) * B + t)) : 0.0;
   double rcol[B];
   int deflated = 0;
 #pragma unroll
@@ -274,52 +287,65 @@ k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, dou
   if (t == 0 && deflated && counters) atomicAdd(&counters[2], (unsigned long long)deflated);
 }
 
+template <int B>
+__global__ void __launch_bounds__(32)
+k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, double* __restrict__ R,
+       double* __restrict__ dinv, unsigned long long* __restrict__ counters) {
+  chol_warp<B>(G1, G2, nq, R, dinv, counters);
+}
+
 // ------------------------------------------------------------------------------------------------
-// P <- P (I - U(E)) with E = G3 - I; block 0 writes (I + U(E)) R1 (upper triangular) to Tdiag
-// and/or Rout, and records max |E| over non-deflated columns in counters[3].
+// P <- P (I - U(E)) with E = G3 - I; (I + U(E)) R1 (upper triangular) goes to Tdiag and/or Rout,
+// and max |E| over non-deflated columns to counters[3].
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(ORTH_T)
-k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* __restrict__ Tdiag, int ldT,
-          double* __restrict__ Rout, double* __restrict__ P, int n, int b, int g,
-          unsigned long long* __restrict__ counters, float* __restrict__ Pf) {
-  __shared__ double sU[OB_MAXB * OB_MAXB];   // U(E)
-  __shared__ double sR[OB_MAXB * OB_MAXB];
+// sU = U(E) (upper triangle of E, halved diagonal), from G3 read through L2.  All threads.
+__device__ __forceinline__ void correct_load_U(const double* __restrict__ G3, int b, double* __restrict__ sU) {
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     int i = e / b, j = e - i * b;
-    double x = G3[e] - (i == j ? 1.0 : 0.0);
+    double x = __ldcg(G3 + e) - (i == j ? 1.0 : 0.0);
     sU[e] = (j > i) ? x : ((i == j) ? 0.5 * x : 0.0);
-    if (blockIdx.x == 0) sR[e] = R1[e];   // only block 0 forms the product with R1
   }
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+}
+
+// (I + U(E)) R1 -> Tdiag / Rout / sRout (any may be NULL); max |E| -> counters[3].  All threads of
+// one CTA; sU, sR1 in shared memory.
+__device__ void correct_coefs(const double* __restrict__ sU, const double* __restrict__ sR1, int b,
+                              double* __restrict__ Tdiag, int ldT, double* __restrict__ Rout,
+                              double* __restrict__ sRout, const double* __restrict__ G3,
+                              unsigned long long* __restrict__ counters) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    int i = e / b, j = e - i * b;
+    double v = 0.0;
+    if (i <= j) {
+      v = sR1[i * b + j];
+      for (int k = i; k <= j; ++k) v += sU[i * b + k] * sR1[k * b + j];
+    }
+    if (Tdiag) Tdiag[i * ldT + j] = v;
+    if (Rout) Rout[e] = v;
+    if (sRout) sRout[e] = v;
+  }
+  if (counters && threadIdx.x < 32) {
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < b * b; e += 32) {
       int i = e / b, j = e - i * b;
-      double v = 0.0;
-      if (i <= j) {
-        v = sR[i * b + j];
-        for (int k = i; k <= j; ++k) v += sU[i * b + k] * sR[k * b + j];
-      }
-      if (Tdiag) Tdiag[i * ldT + j] = v;
-      if (Rout) Rout[e] = v;
+      const double gii = __ldcg(G3 + i * b + i), gjj = __ldcg(G3 + j * b + j);
+      if (gii > 0.5 && gjj > 0.5) mx = fmax(mx, fabs(__ldcg(G3 + e) - (i == j ? 1.0 : 0.0)));
     }
-    if (counters && threadIdx.x < 32) {
-      double mx = 0.0;
-      for (int e = threadIdx.x; e < b * b; e += 32) {
-        int i = e / b, j = e - i * b;
-        if (G3[i * b + i] > 0.5 && G3[j * b + j] > 0.5) mx = fmax(mx, fabs(G3[e] - (i == j ? 1.0 : 0.0)));
-      }
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (threadIdx.x == 0) atomicMax(&counters[3], (unsigned long long)__double_as_longlong(mx));
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) atomicMax(&counters[3], (unsigned long long)__double_as_longlong(mx));
   }
-  const int rows_per_block = ORTH_T / g;
+}
+
+// Rows ib0, ib0 + step, ... (< n) of P <- P (I - U), g lanes per row; Pf: float32 copy.  Uniform
+// trip count for the CTA; row values are exchanged with shuffles so that no lane reads an element
+// another lane has already overwritten.
+__device__ void correct_rows(const double* __restrict__ sU, double* __restrict__ P, int b, int g, int ib0,
+                             int ib_end, int step, float* __restrict__ Pf) {
   const int rl = threadIdx.x / g, d = threadIdx.x - rl * g;
   const int gbase = (threadIdx.x & 31) & ~(g - 1);
-  // uniform trip count for every lane of the block; row values are exchanged with shuffles so
-  // that no lane reads an element another lane has already overwritten
-  for (int ib = blockIdx.x * rows_per_block; ib < n; ib += gridDim.x * rows_per_block) {
+  for (int ib = ib0; ib < ib_end; ib += step) {
     const int i = ib + rl;
-    const bool live = i < n && d < b;
+    const bool live = i < ib_end && d < b;
     const double p = live ? P[(long long)i * b + d] : 0.0;
     double a0 = p, a1 = 0.0;
     for (int k = 0; k < b; ++k) {
@@ -335,6 +361,21 @@ k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* 
       if (Pf) Pf[(long long)i * b + d] = (float)v;
     }
   }
+}
+
+__global__ void __launch_bounds__(ORTH_T)
+k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* __restrict__ Tdiag, int ldT,
+          double* __restrict__ Rout, double* __restrict__ P, int n, int b, int g,
+          unsigned long long* __restrict__ counters, float* __restrict__ Pf) {
+  __shared__ double sU[OB_MAXB * OB_MAXB];   // U(E)
+  __shared__ double sR[OB_MAXB * OB_MAXB];
+  correct_load_U(G3, b, sU);
+  if (blockIdx.x == 0)   // only block 0 forms the product with R1
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) sR[e] = R1[e];
+  __syncthreads();
+  if (blockIdx.x == 0) correct_coefs(sU, sR, b, Tdiag, ldT, Rout, nullptr, G3, counters);
+  const int rows_per_block = ORTH_T / g;
+  correct_rows(sU, P, b, g, blockIdx.x * rows_per_block, n, gridDim.x * rows_per_block, Pf);
 }
 
 int launch_chol(const double* G1, const double* G2, int nq, int b, double* R, double* dinv,
@@ -355,6 +396,214 @@ int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, d
   int blocks = (int)svt_min_ll(svt_ceil_div(n, rows_per_block), 152LL * 8);
   k_correct<<<blocks, ORTH_T, 0, st>>>(G3, R1, Tdiag, ldT, Rout, P, n, b, g, counters, Pf);
   return 1;
+}
+
+// ------------------------------------------------------------------------------------------------
+// The whole orthonormalisation of one block in one cooperative launch.  The launch sequence above
+// (gram, update + gram, Cholesky, update + gram, correction: 8 kernels, each a launch and a pass
+// of memory latency) becomes phases of one kernel separated by grid barriers: every CTA owns a
+// contiguous chunk of rows for all phases; a Gram is formed as per-CTA partials, a barrier, the
+// fixed-order sums spread over all CTAs (one warp per entry), and a barrier; every CTA factors
+// the b x b block itself (the same warp code on the same data gives the same R1 everywhere), so
+// the Cholesky costs no barrier.  Same arithmetic and summation structure as the launch
+// sequence, so the coefficients and the orthonormality level are those of the sequence.
+// ------------------------------------------------------------------------------------------------
+// G[e] = sum over k < nblk of partial[k E + e] for the entries e of this CTA's warps (warp-uniform
+// loop); lane l sums k = l, l + 32, ... and the lanes combine by butterfly: a fixed order.  With
+// Tcol, the coefficient entries e < ncoef also go to Tcol as Gprev + G.  partial and Gprev may have
+// been written by other CTAs of the same kernel: read through L2.
+__device__ void reduce_entries(const double* __restrict__ partial, int nblk, int E, double* __restrict__ G,
+                               const double* __restrict__ Gprev, double* __restrict__ Tcol, int ldT, int ncoef,
+                               int b) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = blockIdx.x * nw + warp; e < E; e += gridDim.x * nw) {
+    double s = 0.0;
+    int k = lane;
+    for (; k + 96 < nblk; k += 128) {
+      const double v0 = __ldcg(partial + (long long)k * E + e);
+      const double v1 = __ldcg(partial + (long long)(k + 32) * E + e);
+      const double v2 = __ldcg(partial + (long long)(k + 64) * E + e);
+      const double v3 = __ldcg(partial + (long long)(k + 96) * E + e);
+      s += (v0 + v1) + (v2 + v3);
+    }
+    for (; k < nblk; k += 32) s += __ldcg(partial + (long long)k * E + e);
+    s = warp_sum(s);
+    if (lane == 0) {
+      G[e] = s;
+      if (Tcol && e < ncoef) {
+        const int i = e / b, j = e - i * b;
+        Tcol[i * ldT + j] = (Gprev ? __ldcg(Gprev + e) : 0.0) + s;
+      }
+    }
+  }
+}
+
+struct OrthCoopArgs {
+  double* P;                  // rows x b, orthonormalised in place
+  const double* Q;            // nq blocks of rows x b, q_stride apart
+  long long q_stride;
+  int nq, n, g, rpc;          // rpc: rows per CTA
+  double *partial, *G1, *G2, *G3;
+  double *Tcol, *Tdiag;       // coefficient outputs (may be NULL), leading dimension ldT
+  int ldT;
+  float* Pf;                  // float32 copy of the result (may be NULL)
+  unsigned long long* counters;
+  unsigned int* err;
+  unsigned int* bar;          // grid barrier word
+  int twoc;                   // second first-order correction
+};
+
+static constexpr size_t orth_coop_smem(int B) {
+  return (size_t)(OB_MAXK * B + 3 * B * B + B) * sizeof(double);
+}
+
+#define SVT_BARRIER_OR_RETURN()                     \
+  do {                                              \
+    if (!svt_grid_barrier(a.bar, a.err)) return;   \
+  } while (0)
+
+template <int B>
+__global__ void __launch_bounds__(ORTH_T) k_orth_coop(OrthCoopArgs a) {
+  extern __shared__ double sm_orth[];
+  double* sC = sm_orth;                 // K x B coefficients (C1, then C2)
+  double* sR = sC + OB_MAXK * B;        // R1
+  double* sU = sR + B * B;              // U(E)
+  double* sR2 = sU + B * B;             // (I + U(E)) R1 of a first correction
+  double* sD = sR2 + B * B;             // 1 / diag(R1)
+  // a barrier of an earlier cooperative kernel gave up: the whole grid returns at once
+  if (*(volatile unsigned int*)a.err & SVT_DEVERR_BARRIER) return;
+  const int K = a.nq * B;
+  const int nb = gridDim.x;
+  const int r0 = blockIdx.x * a.rpc;
+  const int r1 = min(a.n, r0 + a.rpc);
+  if (a.nq > 0) {
+    const int E1 = (a.nq + 1) * B * B;
+    // C1 = Q^T P (with P^T P)
+    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial);
+    SVT_BARRIER_OR_RETURN();
+    reduce_entries(a.partial, nb, E1, a.G1, nullptr, nullptr, 0, 0, B);
+    SVT_BARRIER_OR_RETURN();
+    // P <- P - Q C1; [C2; A] = [Q, P]^T P; coefficients C1 + C2 -> Tcol
+    for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G1 + t);
+    __syncthreads();
+    update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1);
+    __syncthreads();
+    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial);
+    SVT_BARRIER_OR_RETURN();
+    reduce_entries(a.partial, nb, E1, a.G2, a.G1, a.Tcol, a.ldT, K * B, B);
+    SVT_BARRIER_OR_RETURN();
+  } else {
+    gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+    SVT_BARRIER_OR_RETURN();
+    reduce_entries(a.partial, nb, B * B, a.G2, nullptr, nullptr, 0, 0, B);
+    SVT_BARRIER_OR_RETURN();
+  }
+  // R1 = chol(A) in every CTA; P <- (P - Q C2) R1^-1; E = P^T P - I
+  if (threadIdx.x < 32) chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD, blockIdx.x == 0 ? a.counters : nullptr);
+  for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G2 + t);
+  __syncthreads();
+  update_rows(1, a.Q, a.q_stride, a.nq, sC, sR, sD, a.P, B, a.g, r0, r1);
+  __syncthreads();
+  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+  SVT_BARRIER_OR_RETURN();
+  reduce_entries(a.partial, nb, B * B, a.G3, nullptr, nullptr, 0, 0, B);
+  SVT_BARRIER_OR_RETURN();
+  correct_load_U(a.G3, B, sU);
+  __syncthreads();
+  const int step = ORTH_T / a.g;
+  if (!a.twoc) {
+    if (blockIdx.x == 0) correct_coefs(sU, sR, B, a.Tdiag, a.ldT, nullptr, nullptr, a.G3, a.counters);
+    correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
+    return;
+  }
+  // two first-order corrections: P^T P = I up to O(|E|^4)
+  correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2, a.G3, blockIdx.x == 0 ? a.counters : nullptr);
+  correct_rows(sU, a.P, B, a.g, r0, r1, step, nullptr);
+  __syncthreads();
+  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+  SVT_BARRIER_OR_RETURN();
+  reduce_entries(a.partial, nb, B * B, a.G3, nullptr, nullptr, 0, 0, B);
+  SVT_BARRIER_OR_RETURN();
+  correct_load_U(a.G3, B, sU);
+  __syncthreads();
+  if (blockIdx.x == 0) correct_coefs(sU, sR2, B, a.Tdiag, a.ldT, nullptr, nullptr, a.G3, nullptr);
+  correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
+}
+
+#undef SVT_BARRIER_OR_RETURN
+
+template <int B>
+static bool orth_coop_attr() {
+  return cudaFuncSetAttribute(k_orth_coop<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)orth_coop_smem(B)) == cudaSuccess;
+}
+
+template <int B>
+static int orth_coop_blocks_per_sm() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_orth_coop<B>, ORTH_T, orth_coop_smem(B)) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+// Largest co-resident grid of the cooperative kernel for every block size (the same bound is
+// used for all, the smallest of them), capped at two CTAs per SM.  0 if unavailable.
+int orth_coop_init() {
+  static int grid = -1;
+  if (grid >= 0) return grid;
+  int dev = 0, sms = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+    (void)cudaGetLastError();
+    grid = 0;
+    return grid;
+  }
+  if (!orth_coop_attr<8>() || !orth_coop_attr<16>() || !orth_coop_attr<24>() || !orth_coop_attr<32>()) {
+    (void)cudaGetLastError();
+    grid = 0;
+    return grid;
+  }
+  int bps = std::min(std::min(orth_coop_blocks_per_sm<8>(), orth_coop_blocks_per_sm<16>()),
+                     std::min(orth_coop_blocks_per_sm<24>(), orth_coop_blocks_per_sm<32>()));
+  bps = std::min(bps, 2);
+  grid = bps * sms;
+  return grid;
+}
+
+int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int n, int b, double* partial,
+                     double* G1, double* G2, double* G3, double* Tcol, double* Tdiag, int ldT, float* Pf,
+                     unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
+                     cudaStream_t st) {
+  const int gmax = std::min(orth_coop_init(), max_grid);
+  if (gmax <= 0 || n <= 0) return 0;
+  // at least GRAM_SUB rows per CTA, and at most gmax CTAs
+  int rpc = std::max(GRAM_SUB, (n + gmax - 1) / gmax);
+  const int grid = (n + rpc - 1) / rpc;
+  OrthCoopArgs a;
+  a.P = P; a.Q = Q; a.q_stride = q_stride; a.nq = nq; a.n = n; a.g = row_group(b); a.rpc = rpc;
+  a.partial = partial; a.G1 = G1; a.G2 = G2; a.G3 = G3;
+  a.Tcol = Tcol; a.Tdiag = Tdiag; a.ldT = ldT; a.Pf = Pf;
+  a.counters = counters; a.err = err; a.bar = static_cast<unsigned int*>(bar); a.twoc = twoc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(ORTH_T);
+  cfg.dynamicSmemBytes = orth_coop_smem(b);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  switch (b) {
+    case 8: e = cudaLaunchKernelEx(&cfg, k_orth_coop<8>, a); break;
+    case 16: e = cudaLaunchKernelEx(&cfg, k_orth_coop<16>, a); break;
+    case 24: e = cudaLaunchKernelEx(&cfg, k_orth_coop<24>, a); break;
+    case 32: e = cudaLaunchKernelEx(&cfg, k_orth_coop<32>, a); break;
+    default: return 0;
+  }
+  return e == cudaSuccess ? 1 : 0;
 }
 
 }  // namespace svt
