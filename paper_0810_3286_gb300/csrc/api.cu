@@ -61,7 +61,7 @@ struct svt_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   struct ProfNode { int cls; double bytes; cudaEvent_t a, b; };
   struct CycleGraph {
-    int b, J, ycur, twoc;
+    int b, J, ycur, twoc, thick;
     unsigned int prof_mask;
     cudaGraphExec_t exec;
     int64_t launches;
@@ -96,6 +96,7 @@ struct svt_ctx {
   double* Uf = nullptr;             // m x cap: U (unscaled)
   double* Vf = nullptr;             // n x cap: V
   double* Vwarm = nullptr;          // n x kBMax warm start block
+  double* Uwarm = nullptr;          // m x kBMax: left Ritz vectors kept by a thick restart
   // float32 path only: float32 copies of the dense operands of the per-entry kernels (the sparse
   // products read the current basis block, the fused update the factors), written by the kernels
   // that produce the float64 originals
@@ -390,16 +391,39 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
 // Issues one block Golub-Kahan-Lanczos cycle with full reorthogonalisation from the start block in
 // Vb[0] (n x b), ending with the projected SVD and the copy of the Ritz values, residual estimates
 // and the orthonormality defect to pinned host memory.  Only stream operations: it can be captured.
-static svt_status issue_cycle(svt_ctx* c, int b, int J) {
+//
+// thick: a thick restart of the previous cycle (same b and J).  Its b leading Ritz pairs become
+// block 0 (U_0 = U X[:, 0:b], V_0 = V W[:, 0:b]; Y V_0 = U_0 diag(theta) by the Lanczos relation
+// Y V = U T and T = X diag(theta) W^T, so the projection on block 0 is diag(theta)), and the
+// recurrence continues from the previous cycle's residual block V_J, which is orthogonal to all
+// of V and becomes block 1: the cycle computes blocks 1 .. J-1 only.  The Krylov space is the one
+// an explicit restart from V_0 would build (its next block lies in the span of V_J), for two
+// sparse products and three orthonormalisations less.
+static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick) {
   const int m = (int)c->m, n = (int)c->n;
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
-  CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
-  // float32 path: each block's last orthonormalisation kernel also writes its float32 copy
-  // (Vsh / Ush), which the next sparse product reads
-  TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
+  int j0 = 0;
+  if (!thick) {
+    CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
+    TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
+  } else {
+    int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * ((double)m + n) * (K + b), [&] {
+      return launch_basis_combine(c->Ub, su, J, b, m, c->Xl, K, b, nullptr, c->Uwarm, c->st) +
+             launch_basis_combine(c->Vb, sv, J, b, n, c->Wr, K, b, nullptr, c->Vwarm, c->st);
+    });
+    TRY(launched(c, l));
+    // V_J -> block 1 (its float32 copy, written by its orthonormalisation, is still in Vsh);
+    // the Ritz vectors -> block 0
+    CU(c, cudaMemcpyAsync(c->Vb + sv, c->Vb + J * sv, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c->Vb, c->Vwarm, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c->Ub, c->Uwarm, sizeof(double) * su, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
+    TRY(launched(c, launch_set_diagonal(c->T, kKMax, c->theta, b, c->st)));
+    j0 = 1;
+  }
   int l = 0;
-  for (int j = 0; j < J; ++j) {
+  for (int j = j0; j < J; ++j) {
     double* Uj = c->Ub + j * su;
     double* Vj = c->Vb + j * sv;
     l += prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), [&] {
@@ -412,8 +436,8 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J) {
       return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
     });
     TRY(launched(c, l)); l = 0;
-    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr,
-                       j == J - 1 ? nullptr : c->Vsh));
+    // the float32 copy of the last block V_J is kept for a thick restart
+    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr, c->Vsh));
   }
   // S is written with leading dimension kKMax; the projected SVD reads it as b x b with leading
   // dimension b, so compact it first.
@@ -436,12 +460,13 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J) {
   return SVT_OK;
 }
 
-// Captures issue_cycle for this (b, J, Y buffer, correction mode) once and replays it afterwards:
-// one graph launch instead of ~60 kernel launches per cycle.
-static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
+// Captures issue_cycle for this (b, J, Y buffer, correction mode, restart kind) once and replays it
+// afterwards: one graph launch instead of tens of kernel launches per cycle.
+static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick) {
   const int twoc = c->two_corrections ? 1 : 0;
+  const int tk = thick ? 1 : 0;
   for (auto& g : c->graphs)
-    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.prof_mask == c->prof_mask) {
+    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.thick == tk && g.prof_mask == c->prof_mask) {
       CU(c, cudaGraphLaunch(g.exec, c->st));
       c->launches += g.launches;
       // the graph's event-record nodes fire again on every replay: harvest them at the next sync
@@ -451,7 +476,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
   const int64_t l0 = c->launches;
   const size_t p0 = c->prof_pending.size();
   CU(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  svt_status s = issue_cycle(c, b, J);
+  svt_status s = issue_cycle(c, b, J, thick);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->st, &graph);
   const int64_t nl = c->launches - l0;
@@ -480,7 +505,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
     (void)cudaGetLastError();
     return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
   }
-  c->graphs.push_back({b, J, c->ycur, twoc, c->prof_mask, exec, nl, prof});
+  c->graphs.push_back({b, J, c->ycur, twoc, tk, c->prof_mask, exec, nl, prof});
   CU(c, cudaGraphLaunch(exec, c->st));
   c->launches += nl;
   for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.a, pn.b, true});
@@ -488,14 +513,15 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J) {
 }
 
 // One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
-static svt_status lanczos_cycle(svt_ctx* c, int b, int J, const double** theta_h, const double** res_h) {
+static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, const double** theta_h, const double** res_h) {
   if (c->opt.use_graphs) {
-    TRY(run_cycle_graph(c, b, J));
+    TRY(run_cycle_graph(c, b, J, thick));
   } else {
-    TRY(issue_cycle(c, b, J));
+    TRY(issue_cycle(c, b, J, thick));
   }
-  c->last_spmm += 2 * J;
-  c->total_spmm += 2 * J;
+  const int nspmm = 2 * (thick ? J - 1 : J);
+  c->last_spmm += nspmm;
+  c->total_spmm += nspmm;
   c->last_cycles += 1;
   c->total_cycles += 1;
   TRY(sync_and_check(c));
@@ -554,9 +580,11 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   int warm = std::min(c->warm_cols, b);
   TRY(set_start_block(c, b, warm));
   const int max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
+  bool thick = false;   // the next cycle is a thick restart of the previous one
   for (int cyc = 0;; ++cyc) {
     const double *th, *rs;
-    TRY(lanczos_cycle(c, b, J, &th, &rs));
+    TRY(lanczos_cycle(c, b, J, thick, &th, &rs));
+    thick = false;
     const int K = J * b;
     const int s_eff = std::min(s, K);
     // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
@@ -599,8 +627,13 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     if (cyc + 1 >= max_cycles)
       return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
                   max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
-    TRY(keep_ritz(c, b, J, b));
-    TRY(set_start_block(c, b, b));
+    // not converged, same block: continue from the leading Ritz pairs and the residual block
+    if (J >= 2) {
+      thick = true;
+    } else {
+      TRY(keep_ritz(c, b, J, b));
+      TRY(set_start_block(c, b, b));
+    }
   }
 }
 
@@ -809,6 +842,7 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Uf, (size_t)m * cap));
   TRY(dalloc_t(c, &c->Vf, (size_t)n * cap));
   TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
+  TRY(dalloc_t(c, &c->Uwarm, (size_t)m * kBMax));
   if (c->prec == SVT_FP32) {
     const size_t capf = (size_t)((cap + 3) & ~3);
     TRY(dalloc_t(c, &c->Ush, (size_t)m * kBMax));

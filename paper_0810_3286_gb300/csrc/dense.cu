@@ -76,4 +76,18 @@ int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStre
   return 1;
 }
 
+// ------------------------------------------------------------------------------------------------
+// T[i, i] = d[i] for i < b (row-major T, leading dimension ldT).
+// ------------------------------------------------------------------------------------------------
+__global__ void k_set_diagonal(double* __restrict__ T, int ldT, const double* __restrict__ d, int b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < b) T[(long long)i * ldT + i] = d[i];
+}
+
+int launch_set_diagonal(double* T, int ldT, const double* d, int b, cudaStream_t st) {
+  if (b <= 0) return 0;
+  k_set_diagonal<<<1, 32 * ((b + 31) / 32), 0, st>>>(T, ldT, d, b);
+  return 1;
+}
+
 }  // namespace svt

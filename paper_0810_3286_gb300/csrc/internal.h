@@ -118,6 +118,9 @@ int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
                          const double* scale, double* Out, cudaStream_t st, float* OutF = nullptr, int ldF = 0);
 
+// T[i, i] = d[i] for i < b (row-major T, leading dimension ldT).
+int launch_set_diagonal(double* T, int ldT, const double* d, int b, cudaStream_t st);
+
 // Fill an n x b block with uniform(-1, 1) numbers from SplitMix64 (columns c >= c0 only).
 int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStream_t st);
 
