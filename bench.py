@@ -49,6 +49,13 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# Arithmetic peaks derived from GB300's unit counts at the maximum SM clock (2070 MHz, 152 SMs):
+# float64 2 FMA / clock / SM (1.26 TFLOP/s, the nominal 1.25), float32 128 FMA / clock / SM.
+SM_COUNT, SM_MAX_HZ = 152, 2.070e9
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_HZ / 1e12
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_HZ / 1e12
+
+
 def _kernel_source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_0810_3286_gb300", "csrc")
@@ -285,15 +292,17 @@ def run_ours(args):
     value = iters_all / total_s_max
 
     # --- roofline pass: the same steps again with CUDA events (on the library's stream, recorded by
-    # the captured graphs) around every launch of the HBM-streaming kernels ---
-    roof_classes = ("spmm", "spmm_t", "sddmm_update")
+    # the captured graphs) around every launch of every kernel class ---
     prof_timed = {}
+    roof_sweeps, roof_svd = 0.0, 0.0
     for k in range(min(args.steps, 3)):
         l2_flush.zero_()
-        _, _, prof = step_device(roof_classes)
-        for c, (n, ms, by) in prof.items():
-            a = prof_timed.setdefault(c, [0, 0.0, 0.0])
-            a[0] += n; a[1] += ms; a[2] += by
+        _, _, prof = step_device(tuple(_abi.PROF_CLASSES))
+        for c, (n, ms, by, fl) in prof.items():
+            a = prof_timed.setdefault(c, [0, 0.0, 0.0, 0.0])
+            a[0] += n; a[1] += ms; a[2] += by; a[3] += fl
+        roof_sweeps += step_device.counters["jacobi_sweeps"]
+        roof_svd += step_device.counters["svd_calls"]
     torch.cuda.synchronize()
 
     # --- end to end through the C-ABI with host buffers ---
@@ -326,10 +335,11 @@ def run_ours(args):
 
     peak, peak_kind = _peaks()
 
+    def _sum(classes, i):
+        return sum(prof_timed.get(c, [0, 0.0, 0.0, 0.0])[i] for c in classes)
+
     def _roof(classes, name):
-        n_l = sum(prof_timed.get(c, [0, 0, 0])[0] for c in classes)
-        ms_l = sum(prof_timed.get(c, [0, 0, 0])[1] for c in classes)
-        by_l = sum(prof_timed.get(c, [0, 0, 0])[2] for c in classes)
+        n_l, ms_l, by_l = _sum(classes, 0), _sum(classes, 1), _sum(classes, 2)
         achieved = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
         return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": "%s copy bandwidth" % peak_kind,
@@ -337,7 +347,34 @@ def run_ours(args):
                 "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
                 "algorithmic_bytes_per_launch": by_l / n_l if n_l else None}
 
-    roofline = _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)")
+    def _roof_alu(cls, name, flops_total, peak_tflops, kind):
+        n_l, ms_l = _sum((cls,), 0), _sum((cls,), 1)
+        achieved = (flops_total / 1e12) / (ms_l / 1e3) if ms_l > 0 else None
+        return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tflops) if achieved else None,
+                "peak_kind": "%s peak derived from unit counts x maximum SM clock" % kind,
+                "traffic": _traffic_for(cls), "launches_timed": n_l,
+                "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
+                "algorithmic_flops_per_launch": flops_total / n_l if n_l else None}
+
+    # the projected SVD's float32 flops: per sweep (K - 1) rounds of K/2 pair rotations, each three
+    # length-K inner products (6K) and the rotation of two K-columns of G and of W (12K); K = J b
+    Kp = 3 * 16
+    jac_flops = roof_sweeps * (Kp - 1) * (Kp // 2) * 18.0 * Kp
+    rooflines = {
+        "orth": lambda: _roof_alu("orth", "k_orth_coop (block CGS2 + Cholesky QR, float64)", _sum(("orth",), 3),
+                                  PEAK_FP64_TFLOPS, "float64"),
+        "jacobi": lambda: _roof_alu("jacobi", "k_jacobi_mixed (projected SVD, one CTA)", jac_flops,
+                                    PEAK_FP32_TFLOPS, "float32"),
+        "spmm": lambda: _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)"),
+        "spmm_t": lambda: _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)"),
+        "sddmm_update": lambda: _roof(("sddmm_update",), "k_sddmm_update"),
+    }
+    timed_shares = {c: v[1] for c, v in prof_timed.items()}
+    dominant = max(timed_shares, key=lambda c: timed_shares[c]) if timed_shares else "spmm"
+    roofline = rooflines.get(dominant, rooflines["spmm"])()
+    roofline["time_share"] = timed_shares.get(dominant, 0.0) / (sum(timed_shares.values()) or 1.0)
+    roofline_spmm = _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)")
     roofline_update = _roof(("sddmm_update",), "k_sddmm_update")
     cpu = cpu_baseline(args.config, 0, max_iters=1) if not args.no_cpu_baseline else None
     if cpu is not None:
@@ -364,6 +401,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(8 * (p.n1 + p.n2 + 1) * e2e_r)},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "roofline_spmm": roofline_spmm,
         "roofline_update": roofline_update,
         "kernel_time_shares": {k: round(v / tot, 4) for k, v in shares.items()},
         "dominant_kernel_class": dominant_all,

@@ -76,6 +76,9 @@ typedef struct svt_options {
   int fused_orth;         /* 1 (default): each block orthonormalisation runs as one cooperative
                              kernel with grid barriers where the device supports cooperative
                              launches; 0: as a sequence of eight kernels (same arithmetic) */
+  int restart_steps;      /* block steps J of a cycle that thick-restarts a non-converged one (block 0
+                             = the leading Ritz pairs, block 1 = the residual block); 0 = same as
+                             lanczos_steps */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
@@ -256,13 +259,15 @@ int64_t svt_kernel_launches(const svt_ctx* ctx);
  *   supports cooperative launches).
  * svt_set_profile selects the classes whose launches are bracketed by CUDA events on the context
  * stream (0 = none) and clears the totals.  svt_get_profile writes, per class, the number of
- * bracketed launch groups, their total device time in milliseconds and the algorithmic bytes they
- * move (arrays of SVT_PROF_CLASSES entries; any pointer may be NULL).  Both synchronise the stream.
+ * bracketed launch groups, their total device time in milliseconds, the algorithmic bytes they
+ * move and the floating-point operations they perform (flops are counted for SPMM, SPMM_T, SDDMM
+ * and ORTH, 0 for the other classes; arrays of SVT_PROF_CLASSES entries; any pointer may be NULL).
+ * Both synchronise the stream.
  */
 enum { SVT_PROF_SPMM = 0, SVT_PROF_SPMM_T, SVT_PROF_GRAM, SVT_PROF_BLOCK_UPDATE, SVT_PROF_SMALL, SVT_PROF_JACOBI,
        SVT_PROF_COMBINE, SVT_PROF_SDDMM, SVT_PROF_ORTH, SVT_PROF_CLASSES };
 svt_status svt_set_profile(svt_ctx* ctx, unsigned int class_mask);
-svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops);
 
 /*
  * Cumulative solver counters since svt_create, written to out[0 .. min(n, 8)):

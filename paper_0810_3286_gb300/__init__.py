@@ -70,7 +70,8 @@ class Solver:
 
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
-                 max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0):
+                 max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
+                 restart_steps: int = 0):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -84,6 +85,7 @@ class Solver:
         opt.use_graphs = 1 if use_graphs else 0
         opt.fused_orth = 1 if fused_orth else 0
         opt.block = int(block)
+        opt.restart_steps = int(restart_steps)
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda
@@ -233,14 +235,16 @@ class Solver:
         _check(self._L.svt_set_profile(self._ctx, mask), "svt_set_profile", self._ctx)
 
     def profile(self):
-        """{class: (launch groups, total ms, algorithmic bytes)} since the last set_profile."""
+        """{class: (launch groups, total ms, algorithmic bytes, flops)} since the last set_profile."""
         n = len(_abi.PROF_CLASSES)
         launches = np.zeros(n, np.int64)
         ms = np.zeros(n)
         by = np.zeros(n)
-        _check(self._L.svt_get_profile(self._ctx, launches.ctypes.data, ms.ctypes.data, by.ctypes.data),
-               "svt_get_profile", self._ctx)
-        return {c: (int(launches[i]), float(ms[i]), float(by[i])) for i, c in enumerate(_abi.PROF_CLASSES)}
+        fl = np.zeros(n)
+        _check(self._L.svt_get_profile(self._ctx, launches.ctypes.data, ms.ctypes.data, by.ctypes.data,
+                                       fl.ctypes.data), "svt_get_profile", self._ctx)
+        return {c: (int(launches[i]), float(ms[i]), float(by[i]), float(fl[i]))
+                for i, c in enumerate(_abi.PROF_CLASSES)}
 
 
 def sample_omega(m: int, n: int, nnz: int, seed: int, rows_out, cols_out, stream=None) -> None:

@@ -59,9 +59,9 @@ struct svt_ctx {
   cudaStream_t st = nullptr;        // the library's own non-blocking stream (capturable)
   cudaStream_t user_st = nullptr;   // the caller's stream (joined at every call)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  struct ProfNode { int cls; double bytes; cudaEvent_t a, b; };
+  struct ProfNode { int cls; double bytes, flops; cudaEvent_t a, b; };
   struct CycleGraph {
-    int b, J, ycur, twoc, thick;
+    int b, J, ycur, twoc, thick, Jprev;
     unsigned int prof_mask;
     cudaGraphExec_t exec;
     int64_t launches;
@@ -127,10 +127,11 @@ struct svt_ctx {
   // per-kernel-class profile (CUDA events around launches of the classes in prof_mask)
   unsigned int prof_mask = 0;
   std::vector<cudaEvent_t> prof_pool;
-  struct ProfRec { int cls; double bytes; cudaEvent_t a, b; bool graph_owned; };
+  struct ProfRec { int cls; double bytes, flops; cudaEvent_t a, b; bool graph_owned; };
   std::vector<ProfRec> prof_pending;
   double prof_ms[SVT_PROF_CLASSES] = {0};
   double prof_bytes[SVT_PROF_CLASSES] = {0};
+  double prof_flops[SVT_PROF_CLASSES] = {0};
   int64_t prof_n[SVT_PROF_CLASSES] = {0};
 
   // statistics of the last shrink
@@ -211,9 +212,9 @@ static cudaEvent_t prof_event(svt_ctx* c) {
 
 // Runs `f` (which issues the launches of one kernel class and returns their count); when the
 // class is selected by the profile mask, brackets the launches with CUDA events on the context
-// stream and records the algorithmic bytes they move.
+// stream and records the algorithmic bytes they move and the floating-point operations they do.
 template <class F>
-static int prof_launch(svt_ctx* c, int cls, double bytes, F&& f) {
+static int prof_launch_f(svt_ctx* c, int cls, double bytes, double flops, F&& f) {
   if (!(c->prof_mask & (1u << cls))) return f();
   cudaEvent_t a = prof_event(c), b = prof_event(c);
   if (!a || !b) return f();
@@ -225,8 +226,13 @@ static int prof_launch(svt_ctx* c, int cls, double bytes, F&& f) {
   cudaEventRecordWithFlags(a, c->st, flags);
   int n = f();
   cudaEventRecordWithFlags(b, c->st, flags);
-  c->prof_pending.push_back({cls, bytes, a, b, false});
+  c->prof_pending.push_back({cls, bytes, flops, a, b, false});
   return n;
+}
+
+template <class F>
+static int prof_launch(svt_ctx* c, int cls, double bytes, F&& f) {
+  return prof_launch_f(c, cls, bytes, 0.0, f);
 }
 
 // Called after the stream has drained: folds the recorded event pairs into the totals.
@@ -236,6 +242,7 @@ static void prof_harvest(svt_ctx* c) {
     if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
       c->prof_ms[r.cls] += ms;
       c->prof_bytes[r.cls] += r.bytes;
+      c->prof_flops[r.cls] += r.flops;
       c->prof_n[r.cls] += 1;
     } else {
       (void)cudaGetLastError();
@@ -340,7 +347,11 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
     // one cooperative kernel: gram / update / Cholesky / update / correction phases with grid
     // barriers (same arithmetic as the launch sequence below)
     const double bytes = 8.0 * rows * b * (3.0 * (nq + 1) + 2.0 * nq + 3.0);
-    l += prof_launch(c, SVT_PROF_ORTH, bytes, [&] {
+    // float64 flops of the phases: Grams 2 (nq+1) b^2 + 2 (nq+1) b^2 + 2 b^2, updates 2 nq b^2 +
+    // (2 nq + 1) b^2, correction b^2 per row (nq = 0: 6 b^2); a second correction adds 3 b^2
+    const double per_row = (nq > 0 ? 8.0 * nq + 8.0 : 6.0) + (c->two_corrections ? 3.0 : 0.0);
+    const double flops = per_row * (double)rows * b * b;
+    l += prof_launch_f(c, SVT_PROF_ORTH, bytes, flops, [&] {
       return launch_orth_coop(P, Q, q_stride, nq, rows, b, c->gpart, c->G1, c->G2, c->G3, Tcol, Tdiag, kKMax, Pf,
                               c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st);
     });
@@ -398,8 +409,9 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
 // recurrence continues from the previous cycle's residual block V_J, which is orthogonal to all
 // of V and becomes block 1: the cycle computes blocks 1 .. J-1 only.  The Krylov space is the one
 // an explicit restart from V_0 would build (its next block lies in the span of V_J), for two
-// sparse products and three orthonormalisations less.
-static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick) {
+// sparse products and three orthonormalisations less.  Jprev: block steps of the previous cycle
+// (its basis, projected vectors and residual block V_Jprev); the cycle itself may use another J.
+static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
   const int m = (int)c->m, n = (int)c->n;
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
@@ -408,14 +420,15 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick) {
     CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
     TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
   } else {
-    int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * ((double)m + n) * (K + b), [&] {
-      return launch_basis_combine(c->Ub, su, J, b, m, c->Xl, K, b, nullptr, c->Uwarm, c->st) +
-             launch_basis_combine(c->Vb, sv, J, b, n, c->Wr, K, b, nullptr, c->Vwarm, c->st);
+    const int Kp = Jprev * b;
+    int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * ((double)m + n) * (Kp + b), [&] {
+      return launch_basis_combine(c->Ub, su, Jprev, b, m, c->Xl, Kp, b, nullptr, c->Uwarm, c->st) +
+             launch_basis_combine(c->Vb, sv, Jprev, b, n, c->Wr, Kp, b, nullptr, c->Vwarm, c->st);
     });
     TRY(launched(c, l));
-    // V_J -> block 1 (its float32 copy, written by its orthonormalisation, is still in Vsh);
+    // V_Jprev -> block 1 (its float32 copy, written by its orthonormalisation, is still in Vsh);
     // the Ritz vectors -> block 0
-    CU(c, cudaMemcpyAsync(c->Vb + sv, c->Vb + J * sv, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c->Vb + sv, c->Vb + Jprev * sv, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
     CU(c, cudaMemcpyAsync(c->Vb, c->Vwarm, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
     CU(c, cudaMemcpyAsync(c->Ub, c->Uwarm, sizeof(double) * su, cudaMemcpyDeviceToDevice, c->st));
     CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
@@ -426,13 +439,13 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick) {
   for (int j = j0; j < J; ++j) {
     double* Uj = c->Ub + j * su;
     double* Vj = c->Vb + j * sv;
-    l += prof_launch(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), [&] {
+    l += prof_launch_f(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), 2.0 * c->nnz * b, [&] {
       return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, c->Vsh, Uj, m, b, c->st, c->nnz);
     });
     TRY(launched(c, l)); l = 0;
     TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b, c->Ush));
     double* Vn = c->Vb + (j + 1) * sv;
-    l += prof_launch(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b), [&] {
+    l += prof_launch_f(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b), 2.0 * c->nnz * b, [&] {
       return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
     });
     TRY(launched(c, l)); l = 0;
@@ -462,21 +475,23 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick) {
 
 // Captures issue_cycle for this (b, J, Y buffer, correction mode, restart kind) once and replays it
 // afterwards: one graph launch instead of tens of kernel launches per cycle.
-static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick) {
+static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jprev) {
   const int twoc = c->two_corrections ? 1 : 0;
   const int tk = thick ? 1 : 0;
+  const int jp = thick ? Jprev : 0;
   for (auto& g : c->graphs)
-    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.thick == tk && g.prof_mask == c->prof_mask) {
+    if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.thick == tk && g.Jprev == jp &&
+        g.prof_mask == c->prof_mask) {
       CU(c, cudaGraphLaunch(g.exec, c->st));
       c->launches += g.launches;
       // the graph's event-record nodes fire again on every replay: harvest them at the next sync
-      for (auto& pn : g.prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.a, pn.b, true});
+      for (auto& pn : g.prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.flops, pn.a, pn.b, true});
       return SVT_OK;
     }
   const int64_t l0 = c->launches;
   const size_t p0 = c->prof_pending.size();
   CU(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  svt_status s = issue_cycle(c, b, J, thick);
+  svt_status s = issue_cycle(c, b, J, thick, Jprev);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->st, &graph);
   const int64_t nl = c->launches - l0;
@@ -485,7 +500,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick) {
   std::vector<svt_ctx::ProfNode> prof;
   for (size_t i = p0; i < c->prof_pending.size(); ++i) {
     const auto& r = c->prof_pending[i];
-    prof.push_back({r.cls, r.bytes, r.a, r.b});
+    prof.push_back({r.cls, r.bytes, r.flops, r.a, r.b});
   }
   c->prof_pending.resize(p0);
   if (s != SVT_OK || e != cudaSuccess) {
@@ -505,19 +520,20 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick) {
     (void)cudaGetLastError();
     return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
   }
-  c->graphs.push_back({b, J, c->ycur, twoc, tk, c->prof_mask, exec, nl, prof});
+  c->graphs.push_back({b, J, c->ycur, twoc, tk, jp, c->prof_mask, exec, nl, prof});
   CU(c, cudaGraphLaunch(exec, c->st));
   c->launches += nl;
-  for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.a, pn.b, true});
+  for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.flops, pn.a, pn.b, true});
   return SVT_OK;
 }
 
 // One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
-static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, const double** theta_h, const double** res_h) {
+static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, const double** theta_h,
+                                const double** res_h) {
   if (c->opt.use_graphs) {
-    TRY(run_cycle_graph(c, b, J, thick));
+    TRY(run_cycle_graph(c, b, J, thick, Jprev));
   } else {
-    TRY(issue_cycle(c, b, J, thick));
+    TRY(issue_cycle(c, b, J, thick, Jprev));
   }
   const int nspmm = 2 * (thick ? J - 1 : J);
   c->last_spmm += nspmm;
@@ -581,10 +597,12 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   TRY(set_start_block(c, b, warm));
   const int max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
   bool thick = false;   // the next cycle is a thick restart of the previous one
+  int Jprev = 0;        // block steps of the previous cycle
   for (int cyc = 0;; ++cyc) {
     const double *th, *rs;
-    TRY(lanczos_cycle(c, b, J, thick, &th, &rs));
+    TRY(lanczos_cycle(c, b, J, thick, Jprev, &th, &rs));
     thick = false;
+    Jprev = J;
     const int K = J * b;
     const int s_eff = std::min(s, K);
     // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
@@ -627,9 +645,12 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     if (cyc + 1 >= max_cycles)
       return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
                   max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
-    // not converged, same block: continue from the leading Ritz pairs and the residual block
-    if (J >= 2) {
+    // not converged, same block: continue from the leading Ritz pairs and the residual block,
+    // extending the space by restart_steps - 1 blocks
+    const int Jr = std::max(1, std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : J, kKMax / b));
+    if (Jr >= 2) {
       thick = true;
+      J = Jr;
     } else {
       TRY(keep_ritz(c, b, J, b));
       TRY(set_start_block(c, b, b));
@@ -693,6 +714,7 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->seed = 0x5eed5eedULL;
   opt->stream = nullptr;
   opt->fused_orth = 1;
+  opt->restart_steps = 0;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -986,7 +1008,7 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   int r = 0;
   TRY(shrink_current(c, c->tau, c->r + 1, &r));
   const int nxt = 1 - c->ycur;
-  TRY(launched(c, prof_launch(c, SVT_PROF_SDDMM, sddmm_bytes(c, r), [&] {
+  TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, sddmm_bytes(c, r), (2.0 * r + 4.0) * c->nnz, [&] {
     return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
                                c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
                                c->upd_partial, c->dscal, c->err, c->st);
@@ -1345,12 +1367,13 @@ extern "C" svt_status svt_set_profile(svt_ctx* c, unsigned int class_mask) {
   for (int i = 0; i < SVT_PROF_CLASSES; ++i) {
     c->prof_ms[i] = 0.0;
     c->prof_bytes[i] = 0.0;
+    c->prof_flops[i] = 0.0;
     c->prof_n[i] = 0;
   }
   return SVT_OK;
 }
 
-extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms, double* bytes) {
+extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms, double* bytes, double* flops) {
   if (!c) return SVT_ERR_ARG;
   StreamJoin join(c);
   CU(c, cudaStreamSynchronize(c->st));
@@ -1359,6 +1382,7 @@ extern "C" svt_status svt_get_profile(svt_ctx* c, int64_t* launches, double* ms,
     if (launches) launches[i] = c->prof_n[i];
     if (ms) ms[i] = c->prof_ms[i];
     if (bytes) bytes[i] = c->prof_bytes[i];
+    if (flops) flops[i] = c->prof_flops[i];
   }
   return SVT_OK;
 }
