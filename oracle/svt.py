@@ -120,6 +120,39 @@ def rank_policy(sigma: np.ndarray, r_prev: int, tau: float, ell: int):
             return s_eff, passes
 
 
+@dataclasses.dataclass
+class StepResult:
+    """One pass of Algorithm 1's loop body (Sec. 5.1.5) from the dual iterate y."""
+    s_k: int
+    passes: int
+    r_k: int
+    U: np.ndarray
+    d: np.ndarray
+    V: np.ndarray
+    sigma: np.ndarray       # all singular values of Y, decreasing
+    x: np.ndarray           # X^k on Omega
+    e: np.ndarray           # M - X^k on Omega
+    res: float              # ||P_Omega(X^k - M)||_F / ||P_Omega M||_F  (eq. (5.5))
+
+
+def svt_step(n1: int, n2: int, rows, cols, m_vals, y, tau: float, r_prev: int, ell: int,
+             norm_m: float) -> StepResult:
+    """The loop body of Algorithm 1 for the dual iterate y on Omega: the shrink X^k = D_tau(Y^{k-1})
+    by the full SVD (eq. (2.2)) with the s_k path of the rank policy (Sec. 5.1.1), X^k on Omega and
+    the relative residual of eq. (5.5).  The dual step Y^k = Y^{k-1} + delta P_Omega(M - X^k)
+    (eq. (2.7)) is left to the caller, which takes it only when the stopping rule fails."""
+    Y = dense_from_omega(n1, n2, rows, cols, y)
+    Uf, s, Vf = svd(Y)
+    s_k, passes = rank_policy(s, r_prev, tau, ell)
+    r_k = int(np.count_nonzero(s > tau))
+    U, d, V = Uf[:, :r_k], s[:r_k] - tau, Vf[:, :r_k]
+    # X^k on Omega: x_p = sum_j d_j U[i_p, j] V[j_p, j]
+    x = np.einsum("pj,j,pj->p", U[rows], d, V[cols]) if r_k > 0 else np.zeros_like(y)
+    e = m_vals - x
+    res = math.sqrt(float(np.sum(e * e))) / norm_m
+    return StepResult(s_k=s_k, passes=passes, r_k=r_k, U=U, d=d, V=V, sigma=s, x=x, e=e, res=res)
+
+
 def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: float = 1e-4,
         ell: int = 5, k_max: int = 1000, k0: Optional[int] = None, kick: bool = True,
         keep_trace: bool = True, max_iters: Optional[int] = None) -> SVTResult:
@@ -148,23 +181,16 @@ def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: flo
     k = 0
     limit = k_max if max_iters is None else min(k_max, max_iters)
     for k in range(1, limit + 1):
-        Y = dense_from_omega(n1, n2, rows, cols, y)
-        Uf, s, Vf = svd(Y)
-        s_k, passes = rank_policy(s, r_prev, tau, ell)
-        r_k = int(np.count_nonzero(s > tau))
-        U, d, V = Uf[:, :r_k], s[:r_k] - tau, Vf[:, :r_k]
-        # X^k on Omega: x_p = sum_j d_j U[i_p, j] V[j_p, j]
-        x = np.einsum("pj,j,pj->p", U[rows], d, V[cols]) if r_k > 0 else np.zeros_like(y)
-        e = m_vals - x
-        res = math.sqrt(float(np.sum(e * e))) / norm_m
+        st = svt_step(n1, n2, rows, cols, m_vals, y, tau, r_prev, ell, norm_m)
+        U, d, V = st.U, st.d, st.V
         if keep_trace:
-            trace.append(IterRecord(k=k, s_k=s_k, passes=passes, r_k=r_k, res=res, x_omega=x.copy(),
-                                    y_omega=y.copy(), sigma=s[:r_k + ell].copy()))
-        r_prev = r_k
-        if res <= eps:
+            trace.append(IterRecord(k=k, s_k=st.s_k, passes=st.passes, r_k=st.r_k, res=st.res,
+                                    x_omega=st.x.copy(), y_omega=y.copy(), sigma=st.sigma[:st.r_k + ell].copy()))
+        r_prev = st.r_k
+        if st.res <= eps:
             converged = True
             break
-        y = y + delta * e
+        y = y + delta * st.e
     return SVTResult(iters=k, k0=k0, norm2=norm2, converged=converged, U=U, d=d, V=V, y_omega=y, trace=trace)
 
 
