@@ -149,6 +149,18 @@ const char* svt_last_error(const svt_ctx* ctx);
 svt_status svt_configure(svt_ctx* ctx, double tau, double delta, double eps, int max_rank, int64_t k0);
 
 /*
+ * Stopping rule for noisy data (Sec. 5.2.1, noisy model eq. (5.9): B_ij = M_ij + Z_ij on Omega with
+ * Z white Gaussian noise of standard deviation sigma; the values given to svt_create are B).
+ * With sigma > 0, svt_step / svt_solve stop at the first X^k that is consistent with the data,
+ *   ||P_Omega(X^k - B)||_F^2 <= (1 + eps_noise) nnz sigma^2          (eq. (5.10)),
+ * instead of the relative-residual rule eq. (5.5); sigma <= 0 restores eq. (5.5).  eps_noise is
+ * the paper's small parameter (it is not given a value there); it must be >= 0.  The rule stays in
+ * force for later svt_configure / svt_solve calls on the context.
+ * Errors: SVT_ERR_ARG (NULL ctx, eps_noise < 0 or not finite).
+ */
+svt_status svt_set_noise_stop(svt_ctx* ctx, double sigma, double eps_noise);
+
+/*
  * One pass of the for-loop body of Algorithm 1: rank policy s_k = r_{k-1} + 1, then + l until a
  * computed singular value is <= tau (Sec. 5.1.1); X^k = sum_{j<=r_k} (sigma_j - tau) u_j v_j^T;
  * residual eq. (5.5); if residual <= eps returns SVT_STOPPED and leaves Y unchanged (the

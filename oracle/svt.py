@@ -155,12 +155,16 @@ def svt_step(n1: int, n2: int, rows, cols, m_vals, y, tau: float, r_prev: int, e
 
 def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: float = 1e-4,
         ell: int = 5, k_max: int = 1000, k0: Optional[int] = None, kick: bool = True,
-        keep_trace: bool = True, max_iters: Optional[int] = None) -> SVTResult:
+        keep_trace: bool = True, max_iters: Optional[int] = None, noise_sigma: float = 0.0,
+        noise_eps: float = 0.0) -> SVTResult:
     """Algorithm 1 (Sec. 5.1.5) in float64 on a dense copy of the iterate.
 
     kick=False starts from Y^0 = 0 (eq. (2.7) without the kicking device); kick=True uses
     Y^0 = k0 delta P_Omega(M) with k0 from eq. (5.3) unless k0 is given.
     max_iters stops early (a bounded sample for timing); the result is then not converged.
+    noise_sigma > 0: the values are noisy observations B (eq. (5.9)) and the loop stops at the
+    first X^k with ||P_Omega(X^k - B)||_F^2 <= (1 + noise_eps) m sigma^2 (eq. (5.10), m = |Omega|)
+    instead of the relative-residual rule eq. (5.5).
     """
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
@@ -187,7 +191,11 @@ def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: flo
             trace.append(IterRecord(k=k, s_k=st.s_k, passes=st.passes, r_k=st.r_k, res=st.res,
                                     x_omega=st.x.copy(), y_omega=y.copy(), sigma=st.sigma[:st.r_k + ell].copy()))
         r_prev = st.r_k
-        if st.res <= eps:
+        if noise_sigma > 0.0:
+            stop = float(np.sum(st.e * st.e)) <= (1.0 + noise_eps) * len(m_vals) * noise_sigma ** 2
+        else:
+            stop = st.res <= eps
+        if stop:
             converged = True
             break
         y = y + delta * st.e

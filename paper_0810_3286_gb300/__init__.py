@@ -134,6 +134,11 @@ class Solver:
     def configure(self, tau: float = 0.0, delta: float = 0.0, eps: float = 1e-4, max_rank: int = 27, k0: int = -1):
         _check(self._L.svt_configure(self._ctx, tau, delta, eps, max_rank, k0), "svt_configure", self._ctx)
 
+    def set_noise_stop(self, sigma: float, eps_noise: float = 0.0):
+        """Stop at the first X^k with ||P_Omega(X^k - B)||_F^2 <= (1 + eps_noise) |Omega| sigma^2
+        (noisy data, eq. (5.10)); sigma <= 0 restores the relative-residual rule eq. (5.5)."""
+        _check(self._L.svt_set_noise_stop(self._ctx, sigma, eps_noise), "svt_set_noise_stop", self._ctx)
+
     def step(self) -> StepInfo:
         info = svt_step_info()
         st = self._L.svt_step(self._ctx, ctypes.byref(info))

@@ -87,6 +87,7 @@ struct svt_ctx {
   // parameters / state of Algorithm 1
   bool configured = false;
   double tau = 0, delta = 0, eps = 1e-4;
+  double noise_sigma = 0.0, noise_eps = 0.0;   // > 0: the noisy-data stopping rule eq. (5.10)
   int max_rank = 0;
   int64_t k0 = 0, k = 0;
   double norm2 = 0.0;
@@ -1000,6 +1001,15 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
   return sync_and_check(c);
 }
 
+extern "C" svt_status svt_set_noise_stop(svt_ctx* c, double sigma, double eps_noise) {
+  if (!c) return SVT_ERR_ARG;
+  if (!(eps_noise >= 0.0) || !std::isfinite(eps_noise) || !std::isfinite(sigma))
+    return fail(c, SVT_ERR_ARG, "eps_noise must be finite and >= 0, sigma finite");
+  c->noise_sigma = sigma > 0.0 ? sigma : 0.0;
+  c->noise_eps = eps_noise;
+  return SVT_OK;
+}
+
 extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   if (!c) return SVT_ERR_ARG;
   StreamJoin join(c);
@@ -1016,7 +1026,8 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaEventRecord(c->ev1, c->st));
   TRY(sync_and_check(c));
-  const double res = std::sqrt(c->h_pin[3 * kKMax]) / c->normF;
+  const double res2 = c->h_pin[3 * kKMax];
+  const double res = std::sqrt(res2) / c->normF;
   c->k += 1;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -1032,7 +1043,12 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
     info->ms = ms;
   }
   if (!std::isfinite(res)) return fail(c, SVT_ERR_NUMERIC, "residual is not finite");
-  if (res <= c->eps) return SVT_STOPPED;
+  if (c->noise_sigma > 0.0) {
+    // eq. (5.10): ||P_Omega(X^k - B)||_F^2 <= (1 + eps) m sigma^2 with m = |Omega|
+    if (res2 <= (1.0 + c->noise_eps) * (double)c->nnz * c->noise_sigma * c->noise_sigma) return SVT_STOPPED;
+  } else if (res <= c->eps) {
+    return SVT_STOPPED;
+  }
   c->ycur = nxt;
   return SVT_OK;
 }

@@ -168,3 +168,50 @@ def test_recovery_plain_fp64_200(oracle_c1_run):
     assert osvt.relative_error(res.U, res.d, res.V, p.A, p.B) < 1e-3
     ranks = [rec.r_k for rec in res.trace]
     assert max(ranks) == p.r and ranks[-1] == p.r
+
+
+@pytest.mark.parametrize("eps_noise", [0.0, 0.1])
+def test_noisy_stop_full_omega_closed_form(eps_noise):
+    """Noisy data, eq. (5.9)-(5.10), with Omega = all entries: B = M + Z has the SVD
+    U_B diag(sigma_B) V_B^T, every iterate is U_B diag(y) V_B^T with the scalar recurrence on all
+    singular values of B, ||X^k - B||_F^2 = sum_i (sigma_B,i - (y_i - tau)_+)^2, and the loop stops
+    at the first k with that below (1 + eps) m sigma^2."""
+    n1, n2, noise = 9, 8, 0.4
+    sigma = np.array([14.0, 9.0, 6.0])
+    Qu, Qv, M, rows, cols, _ = _full_omega_problem(n1, n2, sigma, 3)
+    rng = np.random.default_rng(11)
+    B = M + noise * rng.standard_normal(M.shape)
+    UB, sB, VBt = np.linalg.svd(B, full_matrices=False)
+    tau, delta = 5.0, 1.2
+    res = osvt.svt(n1, n2, rows, cols, B.ravel().copy(), tau, delta, k_max=500, noise_sigma=noise,
+                   noise_eps=eps_noise)
+    y = math.ceil(tau / (delta * sB[0])) * delta * sB
+    thr = (1.0 + eps_noise) * n1 * n2 * noise ** 2
+    for k in range(1, 501):
+        xs = np.maximum(y - tau, 0.0)
+        assert np.all(np.abs(y - tau) > 1e-8 * tau)
+        if float(np.sum((sB - xs) ** 2)) <= thr:
+            break
+        y = y + delta * (sB - xs)
+    assert res.converged and res.iters == k
+    X_expected = (UB * xs) @ VBt
+    assert np.abs(res.trace[-1].x_omega - X_expected.ravel()).max() <= 1e-10 * sB[0]
+    # the previous iterate was not yet consistent with the data
+    assert np.sum((res.trace[-2].x_omega - B.ravel()) ** 2) > thr
+
+
+@pytest.mark.parametrize("ratio", [1e-2, 1e-1])
+def test_noisy_recovery_error_about_noise_ratio(ratio):
+    """Sec. 5.2.1 (Table 2 and the heuristic after it): with the early stop eq. (5.10), the relative
+    reconstruction error is about the noise ratio ||P_Omega Z||_F / ||P_Omega M||_F (Table 2:
+    0.72 - 0.78 times it for rank 10)."""
+    from svt_inputs import config_problem
+    p0 = config_problem("plain_fp64_200", 0)
+    sig = ratio * np.linalg.norm(p0.vals) / math.sqrt(p0.nnz)
+    p = config_problem("plain_fp64_200", 0, noise_sigma=sig)
+    res = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), noise_sigma=sig,
+                   keep_trace=False)
+    assert res.converged
+    err = osvt.relative_error(res.U, res.d, res.V, p.A, p.B)
+    nr = np.linalg.norm(p.vals - p0.vals) / np.linalg.norm(p0.vals)
+    assert 0.4 * nr <= err <= 1.2 * nr, (err, nr)
