@@ -161,6 +161,27 @@ svt_status svt_configure(svt_ctx* ctx, double tau, double delta, double eps, int
 svt_status svt_set_noise_stop(svt_ctx* ctx, double sigma, double eps_noise);
 
 /*
+ * Matrix Dantzig selector (Sec. 3.3, problem (DS) for matrix completion): minimise tau ||X||_* +
+ * 1/2 ||X||_F^2 subject to |B_ij - X_ij| <= E on Omega (B = the values given to svt_create), by the
+ * SVT iteration (iterDS2) with the multipliers Y_+, Y_- >= 0 of the two one-sided constraints:
+ *   X^k = D_tau(Y_+^{k-1} - Y_-^{k-1}),
+ *   Y_+^k = [Y_+^{k-1} + delta P_Omega((B - X^k) - E)]_+,  Y_-^k = [Y_-^{k-1} + delta P_Omega(-(B - X^k) - E)]_+.
+ * E > 0 switches the context to this iteration (and allocates Y_+ and Y_-, ping-pong); E <= 0
+ * returns to Algorithm 1.  Either way the context must be configured again (svt_configure or
+ * svt_solve).  Readings where the paper is silent:
+ *   kick: the first k steps from Y_+ = Y_- = 0 keep X^k = 0 and give Y_+ - Y_- = k delta soft_E(B)
+ *         with soft_E(b) = sign(b) (|b| - E)_+; svt_configure therefore starts at
+ *         k0 = ceil(tau / (delta ||P_Omega soft_E(B)||_2)) (eq. (5.3) on soft_E(B)),
+ *         Y_+ = k0 delta [B - E]_+, Y_- = k0 delta [-B - E]_+;
+ *   stop: the relative constraint violation ||[|B - X^k| - E]_+||_F / ||P_Omega B||_F <= eps
+ *         (the analogue of eq. (5.5); svt_step_info.residual reports it).  The noisy-data rule of
+ *         svt_set_noise_stop does not apply in this mode.
+ * The float32 path keeps Y_+ and Y_- in float32.  svt_save_state / svt_load_state carry them.
+ * Errors: SVT_ERR_ARG (NULL ctx, E not finite), SVT_ERR_OOM.
+ */
+svt_status svt_set_dantzig(svt_ctx* ctx, double E);
+
+/*
  * One pass of the for-loop body of Algorithm 1: rank policy s_k = r_{k-1} + 1, then + l until a
  * computed singular value is <= tau (Sec. 5.1.1); X^k = sum_{j<=r_k} (sigma_j - tau) u_j v_j^T;
  * residual eq. (5.5); if residual <= eps returns SVT_STOPPED and leaves Y unchanged (the

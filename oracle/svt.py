@@ -8,6 +8,8 @@ Everything follows the paper (Cai, Candes, Shen 2008) step by step in float64:
   shrink          D_tau(Y) = U diag((sigma_i - tau)_+) V^T          Sec. 2.1, eq. (2.2)
                   (full SVD by the oracle's own one-sided Jacobi, then the definition)
   kick_k0         k0 with tau / (delta ||P_Omega M||_2) in (k0 - 1, k0]      Sec. 5.1.3, eq. (5.3)
+  svt_dantzig     the matrix Dantzig selector iteration (iterDS2) of Sec. 3.3 with two clamped
+                  multipliers Y_+, Y_- (linear inequality constraints |B - X| <= E on Omega)
   svt             Algorithm 1 of Sec. 5.1.5: Y^0 = k0 delta P_Omega(M), r_0 = 0, then for
                   k = 1..k_max: the s_k rank policy (Sec. 5.1.1), r_k = #{sigma_j > tau},
                   X^k = sum_{j <= r_k} (sigma_j - tau) u_j v_j^T, stop when
@@ -200,6 +202,84 @@ def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: flo
             break
         y = y + delta * st.e
     return SVTResult(iters=k, k0=k0, norm2=norm2, converged=converged, U=U, d=d, V=V, y_omega=y, trace=trace)
+
+
+def soft_values(vals, E: float):
+    """Entrywise soft threshold sign(b) (|b| - E)_+ of the sampled values."""
+    vals = np.asarray(vals, dtype=np.float64)
+    return np.sign(vals) * np.maximum(np.abs(vals) - E, 0.0)
+
+
+@dataclasses.dataclass
+class DSResult:
+    iters: int
+    k0: int
+    converged: bool
+    U: np.ndarray
+    d: np.ndarray
+    V: np.ndarray
+    yp: np.ndarray
+    ym: np.ndarray
+    trace: List[IterRecord]
+
+
+def svt_dantzig(n1: int, n2: int, rows, cols, b_vals, E: float, tau: float, delta: float, eps: float = 1e-4,
+                ell: int = 5, k_max: int = 1000, k0: Optional[int] = None, kick: bool = True,
+                keep_trace: bool = True) -> DSResult:
+    """SVT for the matrix Dantzig selector (Sec. 3.3, problem (DS)) in matrix completion form,
+    iteration (iterDS2): with Y_+, Y_- >= 0 the multipliers of B - X <= E and X - B <= E on Omega,
+        X^k = D_tau(Y_+^{k-1} - Y_-^{k-1}),
+        Y_+^k = [Y_+^{k-1} + delta P_Omega( (B - X^k) - E)]_+,
+        Y_-^k = [Y_-^{k-1} + delta P_Omega(-(B - X^k) - E)]_+,
+    from Y_+^0 = Y_-^0 = 0, in float64 on dense copies (E constant over Omega).
+
+    Kick (the device of Sec. 5.1.3 carried over): while X^k = 0 the updates give
+    Y_+^k = k delta [B - E]_+ and Y_-^k = k delta [-B - E]_+ exactly, so Y_+ - Y_- = k delta soft_E(B);
+    with kick=True the loop starts after k0 such steps, k0 from eq. (5.3) with ||P_Omega soft_E(B)||_2.
+    Stop: the relative constraint violation ||[|B - X^k| - E]_+||_F / ||P_Omega B||_F <= eps (the
+    analogue of eq. (5.5): zero exactly when X^k is feasible); the multipliers are then left at
+    step k - 1 as in Algorithm 1.  IterRecord.res holds that violation.
+    """
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    b = np.asarray(b_vals, dtype=np.float64)
+    norm_b = math.sqrt(float(np.sum(b * b)))
+    soft = soft_values(b, E)
+    if kick:
+        if k0 is None:
+            k0 = kick_k0(tau, delta, spectral_norm(n1, n2, rows, cols, soft))
+        yp = k0 * delta * np.maximum(b - E, 0.0)
+        ym = k0 * delta * np.maximum(-b - E, 0.0)
+    else:
+        k0 = 0
+        yp = np.zeros_like(b)
+        ym = np.zeros_like(b)
+    r_prev = 0
+    trace: List[IterRecord] = []
+    converged = False
+    U = np.zeros((n1, 0)); d = np.zeros(0); V = np.zeros((n2, 0))
+    k = 0
+    for k in range(1, k_max + 1):
+        y = yp - ym
+        Y = dense_from_omega(n1, n2, rows, cols, y)
+        Uf, s, Vf = svd(Y)
+        s_k, passes = rank_policy(s, r_prev, tau, ell)
+        r_k = int(np.count_nonzero(s > tau))
+        U, d, V = Uf[:, :r_k], s[:r_k] - tau, Vf[:, :r_k]
+        x = np.einsum("pj,j,pj->p", U[rows], d, V[cols]) if r_k > 0 else np.zeros_like(b)
+        e = b - x
+        viol = np.maximum(np.abs(e) - E, 0.0)
+        res = math.sqrt(float(np.sum(viol * viol))) / norm_b
+        if keep_trace:
+            trace.append(IterRecord(k=k, s_k=s_k, passes=passes, r_k=r_k, res=res, x_omega=x.copy(),
+                                    y_omega=y.copy(), sigma=s[:r_k + ell].copy()))
+        r_prev = r_k
+        if res <= eps:
+            converged = True
+            break
+        yp = np.maximum(yp + delta * (e - E), 0.0)
+        ym = np.maximum(ym + delta * (-e - E), 0.0)
+    return DSResult(iters=k, k0=k0, converged=converged, U=U, d=d, V=V, yp=yp, ym=ym, trace=trace)
 
 
 def relative_error(U: np.ndarray, d: np.ndarray, V: np.ndarray, A: np.ndarray, B: np.ndarray) -> float:

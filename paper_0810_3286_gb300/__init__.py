@@ -139,6 +139,11 @@ class Solver:
         (noisy data, eq. (5.10)); sigma <= 0 restores the relative-residual rule eq. (5.5)."""
         _check(self._L.svt_set_noise_stop(self._ctx, sigma, eps_noise), "svt_set_noise_stop", self._ctx)
 
+    def set_dantzig(self, E: float):
+        """Matrix Dantzig selector (Sec. 3.3): constraints |B - X| <= E on Omega, multipliers Y_+ and
+        Y_- (iteration (iterDS2)); E <= 0 returns to Algorithm 1.  Configure again afterwards."""
+        _check(self._L.svt_set_dantzig(self._ctx, E), "svt_set_dantzig", self._ctx)
+
     def step(self) -> StepInfo:
         info = svt_step_info()
         st = self._L.svt_step(self._ctx, ctypes.byref(info))

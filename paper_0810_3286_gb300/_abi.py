@@ -113,6 +113,7 @@ PROTOTYPES = {
     "svt_load_state": (ctypes.c_int, [_ctxp, _vp, ctypes.c_size_t]),
     "svt_kernel_launches": (ctypes.c_int64, [_ctxp]),
     "svt_set_profile": (ctypes.c_int, [_ctxp, ctypes.c_uint]),
+    "svt_set_dantzig": (ctypes.c_int, [_ctxp, ctypes.c_double]),
     "svt_set_noise_stop": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.c_double]),
     "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, _vp]),
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),

@@ -88,6 +88,9 @@ struct svt_ctx {
   bool configured = false;
   double tau = 0, delta = 0, eps = 1e-4;
   double noise_sigma = 0.0, noise_eps = 0.0;   // > 0: the noisy-data stopping rule eq. (5.10)
+  double ds_E = 0.0;                // > 0: matrix Dantzig selector (iterDS2) with tolerance E
+  void* Yp[2] = {nullptr, nullptr}; // its multipliers Y_+ and Y_- (ping-pong, row-major order)
+  void* Ym[2] = {nullptr, nullptr};
   int max_rank = 0;
   int64_t k0 = 0, k = 0;
   double norm2 = 0.0;
@@ -979,26 +982,52 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
   c->eps = eps > 0 ? eps : 1e-4;
   c->max_rank = max_rank;
   if (!std::isfinite(c->tau) || !std::isfinite(c->delta)) return fail(c, SVT_ERR_ARG, "tau/delta not finite");
-  // ||P_Omega M||_2: leading singular value of Y = P_Omega M (Lanczos, s = 1)
+  // ||P_Omega M||_2: leading singular value of Y = P_Omega M (Lanczos, s = 1); for the Dantzig
+  // selector the operand of the first shrinks is k delta soft_E(B) instead (see svt_set_dantzig)
   c->ycur = 0;
   c->warm_cols = 0;
-  TRY(launched(c, launch_scale_values(c->prec, c->Mv, 1.0, c->Ycsr[0], c->Ycsc[0], c->csr_to_csc, c->nnz, c->st)));
+  if (c->ds_E > 0.0)
+    TRY(launched(c, launch_dual_kick(c->prec, c->Mv, 1.0, c->ds_E, c->Ycsr[0], c->Ycsc[0], nullptr, nullptr,
+                                     c->csr_to_csc, c->nnz, c->st)));
+  else
+    TRY(launched(c, launch_scale_values(c->prec, c->Mv, 1.0, c->Ycsr[0], c->Ycsc[0], c->csr_to_csc, c->nnz, c->st)));
   std::vector<double> th;
   int s = 0, passes = 0, b = 0, J = 0;
   // huge tau so that the rank policy stops after the first converged triplet
   TRY(partial_svd(c, 1, INFINITY, th, &s, &passes, &b, &J, /*strict=*/true));
   c->norm2 = th.empty() ? 0.0 : th[0];
-  if (!(c->norm2 > 0.0)) return fail(c, SVT_ERR_NUMERIC, "||P_Omega M||_2 is zero");
+  if (!(c->norm2 > 0.0))
+    return fail(c, SVT_ERR_NUMERIC, c->ds_E > 0.0 ? "soft_E(B) is zero: X = 0 already meets |B - X| <= E"
+                                                  : "||P_Omega M||_2 is zero");
   TRY(keep_ritz(c, b, J, std::min(b, 8)));
   if (k0 >= 0) c->k0 = k0;
   else c->k0 = (int64_t)std::ceil(c->tau / (c->delta * c->norm2));
-  TRY(launched(c, launch_scale_values(c->prec, c->Mv, (double)c->k0 * c->delta, c->Ycsr[0], c->Ycsc[0],
-                                      c->csr_to_csc, c->nnz, c->st)));
+  if (c->ds_E > 0.0)
+    TRY(launched(c, launch_dual_kick(c->prec, c->Mv, (double)c->k0 * c->delta, c->ds_E, c->Ycsr[0], c->Ycsc[0],
+                                     c->Yp[0], c->Ym[0], c->csr_to_csc, c->nnz, c->st)));
+  else
+    TRY(launched(c, launch_scale_values(c->prec, c->Mv, (double)c->k0 * c->delta, c->Ycsr[0], c->Ycsc[0],
+                                        c->csr_to_csc, c->nnz, c->st)));
   c->r = 0;
   c->k = 0;
   c->d_host.clear();
   c->configured = true;
   return sync_and_check(c);
+}
+
+extern "C" svt_status svt_set_dantzig(svt_ctx* c, double E) {
+  if (!c) return SVT_ERR_ARG;
+  if (!std::isfinite(E)) return fail(c, SVT_ERR_ARG, "E must be finite");
+  StreamJoin join(c);
+  if (E > 0.0) {
+    for (int i = 0; i < 2; ++i) {
+      if (!c->Yp[i]) TRY(dalloc(c, &c->Yp[i], c->nnz * c->vbytes));
+      if (!c->Ym[i]) TRY(dalloc(c, &c->Ym[i], c->nnz * c->vbytes));
+    }
+  }
+  c->ds_E = E > 0.0 ? E : 0.0;
+  c->configured = false;   // the multipliers exist only after the next svt_configure / svt_solve
+  return SVT_OK;
 }
 
 extern "C" svt_status svt_set_noise_stop(svt_ctx* c, double sigma, double eps_noise) {
@@ -1018,10 +1047,12 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   int r = 0;
   TRY(shrink_current(c, c->tau, c->r + 1, &r));
   const int nxt = 1 - c->ycur;
-  TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, sddmm_bytes(c, r), (2.0 * r + 4.0) * c->nnz, [&] {
+  SddmmDual dual{c->Yp[c->ycur], c->Ym[c->ycur], c->Yp[nxt], c->Ym[nxt], c->ds_E};
+  const double upd_bytes = sddmm_bytes(c, r) + (c->ds_E > 0.0 ? 4.0 * c->nnz * c->vbytes - c->nnz * c->vbytes : 0.0);
+  TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, upd_bytes, (2.0 * r + 4.0) * c->nnz, [&] {
     return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
                                c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
-                               c->upd_partial, c->dscal, c->err, c->st);
+                               c->upd_partial, c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr);
   })));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaEventRecord(c->ev1, c->st));
@@ -1043,7 +1074,7 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
     info->ms = ms;
   }
   if (!std::isfinite(res)) return fail(c, SVT_ERR_NUMERIC, "residual is not finite");
-  if (c->noise_sigma > 0.0) {
+  if (c->noise_sigma > 0.0 && !(c->ds_E > 0.0)) {
     // eq. (5.10): ||P_Omega(X^k - B)||_F^2 <= (1 + eps) m sigma^2 with m = |Omega|
     if (res2 <= (1.0 + c->noise_eps) * (double)c->nnz * c->noise_sigma * c->noise_sigma) return SVT_STOPPED;
   } else if (res <= c->eps) {
@@ -1303,11 +1334,12 @@ struct StateHeader {
   double tau, delta, eps, norm2;
   int32_t max_rank, flags;   // flags bit 0: two orthonormality corrections
   uint64_t rng_counter;
+  double noise_sigma, noise_eps, ds_E;   // stopping rule eq. (5.10); Dantzig selector tolerance
 };
 
 static size_t state_bytes(const svt_ctx* c) {
   return sizeof(StateHeader) + c->nnz * c->vbytes + sizeof(double) * (size_t)c->r * (1 + c->m + c->m + c->n) +
-         sizeof(double) * (size_t)c->n * c->warm_cols;
+         sizeof(double) * (size_t)c->n * c->warm_cols + (c->ds_E > 0.0 ? 2 * c->nnz * c->vbytes : 0);
 }
 
 extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
@@ -1321,6 +1353,7 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   h.warm_cols = c->warm_cols; h.configured = c->configured; h.k0 = c->k0; h.k = c->k; h.tau = c->tau;
   h.delta = c->delta; h.eps = c->eps; h.norm2 = c->norm2; h.max_rank = c->max_rank; h.rng_counter = c->rng_counter;
   h.flags = c->two_corrections ? 1 : 0;
+  h.noise_sigma = c->noise_sigma; h.noise_eps = c->noise_eps; h.ds_E = c->ds_E;
   char* p = (char*)buf;
   std::memcpy(p, &h, sizeof h); p += sizeof h;
   CU(c, cudaMemcpyAsync(p, ycur_csr(c), c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st)); p += c->nnz * c->vbytes;
@@ -1329,6 +1362,11 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   CU(c, cudaMemcpyAsync(p, c->Uf, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->m * c->r;
   CU(c, cudaMemcpyAsync(p, c->Vf, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->n * c->r;
   CU(c, cudaMemcpyAsync(p, c->Vwarm, sizeof(double) * c->n * c->warm_cols, cudaMemcpyDeviceToHost, c->st));
+  p += sizeof(double) * c->n * c->warm_cols;
+  if (c->ds_E > 0.0) {
+    CU(c, cudaMemcpyAsync(p, c->Yp[c->ycur], c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st)); p += c->nnz * c->vbytes;
+    CU(c, cudaMemcpyAsync(p, c->Ym[c->ycur], c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st));
+  }
   CU(c, cudaStreamSynchronize(c->st));
   *bytes = need;
   return SVT_OK;
@@ -1348,6 +1386,12 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
   c->tau = h.tau; c->delta = h.delta; c->eps = h.eps; c->norm2 = h.norm2; c->max_rank = h.max_rank;
   c->rng_counter = h.rng_counter;
   c->two_corrections = (h.flags & 1) != 0;
+  if (!std::isfinite(h.ds_E) || !std::isfinite(h.noise_sigma) || !std::isfinite(h.noise_eps))
+    return fail(c, SVT_ERR_ARG, "corrupt state");
+  if (h.ds_E > 0.0) TRY(svt_set_dantzig(c, h.ds_E));
+  else c->ds_E = 0.0;
+  c->configured = h.configured != 0;
+  c->noise_sigma = h.noise_sigma; c->noise_eps = h.noise_eps;
   if (bytes < state_bytes(c)) return fail(c, SVT_ERR_ARG, "state buffer too small");
   const char* p = (const char*)buf + sizeof h;
   CU(c, cudaMemcpyAsync(ycur_csr(c), p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st)); p += c->nnz * c->vbytes;
@@ -1356,6 +1400,11 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
   CU(c, cudaMemcpyAsync(c->Uf, p, sizeof(double) * c->m * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->m * c->r;
   CU(c, cudaMemcpyAsync(c->Vf, p, sizeof(double) * c->n * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->n * c->r;
   CU(c, cudaMemcpyAsync(c->Vwarm, p, sizeof(double) * c->n * c->warm_cols, cudaMemcpyHostToDevice, c->st));
+  p += sizeof(double) * c->n * c->warm_cols;
+  if (c->ds_E > 0.0) {
+    CU(c, cudaMemcpyAsync(c->Yp[c->ycur], p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st)); p += c->nnz * c->vbytes;
+    CU(c, cudaMemcpyAsync(c->Ym[c->ycur], p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st));
+  }
   // rebuild the column-major copy of Y from the row-major values
   if (c->prec == SVT_FP64)
     TRY(launched(c, launch_gather_f64((const double*)ycur_csr(c), c->csc_to_csr, c->nnz, (double*)ycur_csc(c), c->st)));

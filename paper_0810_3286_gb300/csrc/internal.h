@@ -129,10 +129,25 @@ int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStre
 //   y_out_csc[csr_to_csc[p]] = y_out[p] (if y_out_csc);  res2 = sum e^2 (deterministic).
 // Factors: float64 Ut (m x r) and V (n x r), or, for precision 1 when Utf and Vf32 are given,
 // float32 copies with leading dimension ldf (a multiple of 4, >= r).
+// dual (may be NULL): the two-multiplier form of the matrix Dantzig selector (iteration (iterDS2)):
+//   yp_out = [yp_in + delta (e - E)]_+, ym_out = [ym_in + delta (-e - E)]_+, y_out = yp_out - ym_out,
+//   res2 = sum [|e| - E]_+^2; y_in is unused.  Needs the float32 factor copies when precision is 1.
+struct SddmmDual {
+  const void* yp_in;
+  const void* ym_in;
+  void* yp_out;
+  void* ym_out;
+  double E;
+};
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
-                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st);
+                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
+                        const SddmmDual* dual = nullptr);
+// y = alpha soft_E(B) (plus the column-major copy), yp = alpha [B - E]_+, ym = alpha [-B - E]_+
+// (any of y_csc, yp, ym may be NULL).
+int launch_dual_kick(int precision, const void* B, double alpha, double E, void* y, void* y_csc, void* yp, void* ym,
+                     const int32_t* csr_to_csc, long long nnz, cudaStream_t st);
 int sddmm_partial_doubles();
 // The same fused kernel (float64 values, no column-major copy) on `blocks` CTAs of 256 threads,
 // one partial sum per CTA in `partial`, the fixed-order total in *res2 (device).

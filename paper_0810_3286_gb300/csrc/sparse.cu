@@ -169,15 +169,28 @@ int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const voi
 static constexpr int UPD_THREADS = 256;
 static constexpr int UPD_BLOCKS = 152 * 8;
 
+// DS (the matrix Dantzig selector, iteration (iterDS2) of Sec. 3.3): the two multipliers Y_+, Y_- of
+// the constraints B - X <= E and X - B <= E are updated as Y_+' = [Y_+ + delta (e - E)]_+ and
+// Y_-' = [Y_- + delta (-e - E)]_+ (e = B - X), the operand of the next shrink is Y_+' - Y_-', and the
+// reduction sums the constraint violation [|e| - E]_+^2 instead of e^2.
+template <typename VT>
+struct DualArgs {
+  const VT* yp_in;
+  const VT* ym_in;
+  VT* yp_out;
+  VT* ym_out;
+  double E;
+};
+
 // RMAX: compile-time bound on r (16, 32 or 64) so that the gathered row V[j, :] lives in registers:
 // all loads of a lane are issued before the dot product, one gather round trip per entry.
-template <typename VT, typename AT, typename FT, int RMAX>
+template <typename VT, typename AT, typename FT, int RMAX, bool DS>
 __global__ void __launch_bounds__(UPD_THREADS)
 k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col_idx,
                const int32_t* __restrict__ csr_to_csc, const VT* __restrict__ M, const VT* __restrict__ y_in,
                VT* __restrict__ y_out, VT* __restrict__ y_out_csc, const FT* __restrict__ Ut,
                const FT* __restrict__ V, int r, int ldf, int n_rows, AT delta, double* __restrict__ partial,
-               unsigned int* err) {
+               unsigned int* err, DualArgs<VT> ds) {
   __shared__ double red[UPD_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -205,7 +218,13 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
         for (int t = 0; t < RMAX; ++t) vr[t] = (live && t < r) ? __ldg(vj + t) : (FT)0;
       }
       const AT mp = live ? (AT)M[p] : (AT)0;
-      const AT yp = live ? (AT)y_in[p] : (AT)0;
+      AT yp = (AT)0, ypl = (AT)0, ymi = (AT)0;
+      if constexpr (DS) {
+        ypl = live ? (AT)ds.yp_in[p] : (AT)0;
+        ymi = live ? (AT)ds.ym_in[p] : (AT)0;
+      } else {
+        yp = live ? (AT)y_in[p] : (AT)0;
+      }
       const int q = (live && y_out_csc) ? csr_to_csc[p] : 0;
       AT x0 = 0, x1 = 0;
 #pragma unroll
@@ -217,10 +236,23 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
       }
       if (live) {
         AT ev = mp - (x0 + x1);
-        VT yn = (VT)(yp + delta * ev);
-        y_out[p] = yn;
-        if (y_out_csc) y_out_csc[q] = yn;
-        acc += ev * ev;
+        if constexpr (DS) {
+          const AT E = (AT)ds.E;
+          const AT ypn = fmax(ypl + delta * (ev - E), (AT)0);
+          const AT ymn = fmax(ymi + delta * (-ev - E), (AT)0);
+          ds.yp_out[p] = (VT)ypn;
+          ds.ym_out[p] = (VT)ymn;
+          const VT yn = (VT)(ypn - ymn);
+          y_out[p] = yn;
+          if (y_out_csc) y_out_csc[q] = yn;
+          const AT v = fmax(fabs(ev) - E, (AT)0);
+          acc += v * v;
+        } else {
+          VT yn = (VT)(yp + delta * ev);
+          y_out[p] = yn;
+          if (y_out_csc) y_out_csc[q] = yn;
+          acc += ev * ev;
+        }
       }
     }
   }
@@ -253,40 +285,58 @@ __global__ void k_sum_fixed(const double* __restrict__ partial, int np, double* 
 
 int sddmm_partial_doubles() { return UPD_BLOCKS; }
 
-template <typename VT, typename AT, typename FT>
+template <typename VT, typename AT, typename FT, bool DS>
 static void sddmm_dispatch(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc, const VT* M,
                            const VT* y_in, VT* y_out, VT* y_out_csc, const FT* Ut, const FT* V, int r, int ldf,
-                           int n_rows, AT delta, int blocks, double* partial, unsigned int* err, cudaStream_t st) {
+                           int n_rows, AT delta, int blocks, double* partial, unsigned int* err, cudaStream_t st,
+                           DualArgs<VT> ds) {
   if (r <= 16)
-    k_sddmm_update<VT, AT, FT, 16><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
-                                                                    err);
+    k_sddmm_update<VT, AT, FT, 16, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
   else if (r <= 32)
-    k_sddmm_update<VT, AT, FT, 32><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
-                                                                    err);
+    k_sddmm_update<VT, AT, FT, 32, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
   else
-    k_sddmm_update<VT, AT, FT, 64><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M, y_in, y_out,
-                                                                    y_out_csc, Ut, V, r, ldf, n_rows, delta, partial,
-                                                                    err);
+    k_sddmm_update<VT, AT, FT, 64, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
 }
 
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
-                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st) {
-  if (precision == 0)
-    sddmm_dispatch<double, double, double>(row_ptr, col_idx, csr_to_csc, (const double*)M, (const double*)y_in,
-                                           (double*)y_out, (double*)y_out_csc, Ut, V, r, r, n_rows, delta,
-                                           UPD_BLOCKS, partial, err, st);
-  else if (Utf && Vf32)
-    sddmm_dispatch<float, float, float>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
-                                        (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows, (float)delta,
-                                        UPD_BLOCKS, partial, err, st);
-  else
-    sddmm_dispatch<float, float, double>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
-                                         (float*)y_out, (float*)y_out_csc, Ut, V, r, r, n_rows, (float)delta,
-                                         UPD_BLOCKS, partial, err, st);
+                        double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
+                        const SddmmDual* dual) {
+  if (precision == 0) {
+    DualArgs<double> ds{};
+    if (dual) {
+      ds = {(const double*)dual->yp_in, (const double*)dual->ym_in, (double*)dual->yp_out, (double*)dual->ym_out, dual->E};
+      sddmm_dispatch<double, double, double, true>(row_ptr, col_idx, csr_to_csc, (const double*)M, nullptr,
+                                                   (double*)y_out, (double*)y_out_csc, Ut, V, r, r, n_rows, delta,
+                                                   UPD_BLOCKS, partial, err, st, ds);
+    } else {
+      sddmm_dispatch<double, double, double, false>(row_ptr, col_idx, csr_to_csc, (const double*)M,
+                                                    (const double*)y_in, (double*)y_out, (double*)y_out_csc, Ut, V,
+                                                    r, r, n_rows, delta, UPD_BLOCKS, partial, err, st, ds);
+    }
+  } else if (Utf && Vf32) {
+    DualArgs<float> ds{};
+    if (dual) {
+      ds = {(const float*)dual->yp_in, (const float*)dual->ym_in, (float*)dual->yp_out, (float*)dual->ym_out, dual->E};
+      sddmm_dispatch<float, float, float, true>(row_ptr, col_idx, csr_to_csc, (const float*)M, nullptr,
+                                                (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
+                                                (float)delta, UPD_BLOCKS, partial, err, st, ds);
+    } else {
+      sddmm_dispatch<float, float, float, false>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
+                                                 (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
+                                                 (float)delta, UPD_BLOCKS, partial, err, st, ds);
+    }
+  } else {
+    if (dual) return 0;   // the two-multiplier form runs only with the float32 copies of the factors
+    DualArgs<float> ds{};
+    sddmm_dispatch<float, float, double, false>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
+                                                (float*)y_out, (float*)y_out_csc, Ut, V, r, r, n_rows, (float)delta,
+                                                UPD_BLOCKS, partial, err, st, ds);
+  }
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, UPD_BLOCKS, res2);
   return 2;
 }
@@ -312,6 +362,36 @@ int launch_scale_values(int precision, const void* M, double alpha, void* y, voi
     k_scale_values<double><<<blocks, 256, 0, st>>>((const double*)M, alpha, (double*)y, (double*)y_csc, csr_to_csc, nnz);
   else
     k_scale_values<float><<<blocks, 256, 0, st>>>((const float*)M, alpha, (float*)y, (float*)y_csc, csr_to_csc, nnz);
+  return 1;
+}
+
+// Dantzig-selector kick (Sec. 3.3 with the device of Sec. 5.1.3): y = alpha soft_E(B) (row-major and
+// column-major), and, when yp / ym are given, yp = alpha [B - E]_+ and ym = alpha [-B - E]_+.
+template <typename VT>
+__global__ void k_dual_kick(const VT* __restrict__ B, double alpha, double E, VT* __restrict__ y,
+                            VT* __restrict__ y_csc, VT* __restrict__ yp, VT* __restrict__ ym,
+                            const int32_t* __restrict__ csr_to_csc, long long nnz) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) {
+    const double b = (double)B[p];
+    const double up = fmax(b - E, 0.0), dn = fmax(-b - E, 0.0);
+    const VT v = (VT)(alpha * up - alpha * dn);
+    y[p] = v;
+    if (y_csc) y_csc[csr_to_csc[p]] = v;
+    if (yp) yp[p] = (VT)(alpha * up);
+    if (ym) ym[p] = (VT)(alpha * dn);
+  }
+}
+
+int launch_dual_kick(int precision, const void* B, double alpha, double E, void* y, void* y_csc, void* yp, void* ym,
+                     const int32_t* csr_to_csc, long long nnz, cudaStream_t st) {
+  int blocks = (int)svt_min_ll(svt_ceil_div(nnz, 256), 152LL * 16);
+  if (blocks < 1) return 0;
+  if (precision == 0)
+    k_dual_kick<double><<<blocks, 256, 0, st>>>((const double*)B, alpha, E, (double*)y, (double*)y_csc, (double*)yp,
+                                                (double*)ym, csr_to_csc, nnz);
+  else
+    k_dual_kick<float><<<blocks, 256, 0, st>>>((const float*)B, alpha, E, (float*)y, (float*)y_csc, (float*)yp,
+                                               (float*)ym, csr_to_csc, nnz);
   return 1;
 }
 
@@ -361,8 +441,8 @@ namespace svt {
 int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, const double* M, const double* y_in,
                              double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
                              int blocks, double* partial, double* res2, cudaStream_t st) {
-  sddmm_dispatch<double, double, double>(row_ptr, col_idx, nullptr, M, y_in, y_out, nullptr, Ut, V, r, r, n_rows,
-                                         delta, blocks, partial, nullptr, st);
+  sddmm_dispatch<double, double, double, false>(row_ptr, col_idx, nullptr, M, y_in, y_out, nullptr, Ut, V, r, r,
+                                                n_rows, delta, blocks, partial, nullptr, st, DualArgs<double>{});
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, blocks, res2);
   return 2;
 }

@@ -215,3 +215,54 @@ def test_noisy_recovery_error_about_noise_ratio(ratio):
     err = osvt.relative_error(res.U, res.d, res.V, p.A, p.B)
     nr = np.linalg.norm(p.vals - p0.vals) / np.linalg.norm(p0.vals)
     assert 0.4 * nr <= err <= 1.2 * nr, (err, nr)
+
+
+def _ds_problem(n1, n2, r, m, seed, noise):
+    from svt_inputs import planted_problem
+    return planted_problem(n1, n2, r, m, seed, noise_sigma=noise)
+
+
+def test_dantzig_kick_identity():
+    """Un-kicked Dantzig iteration from Y_+ = Y_- = 0: X^k = 0 and Y_+ - Y_- = k delta soft_E(B) for
+    k <= k0, after which it continues exactly as the kicked run."""
+    p = _ds_problem(20, 16, 2, 180, 4, 0.3)
+    E = 0.2
+    tau, delta = p.tau_default(), p.delta_default()
+    kicked = osvt.svt_dantzig(p.n1, p.n2, p.rows, p.cols, p.vals, E, tau, delta, eps=1e-3, k_max=60)
+    k0 = kicked.k0
+    assert k0 >= 2
+    plain = osvt.svt_dantzig(p.n1, p.n2, p.rows, p.cols, p.vals, E, tau, delta, eps=1e-3, k_max=60 + k0, kick=False)
+    soft = osvt.soft_values(p.vals, E)
+    for k in range(k0 - 1):     # iterates 1 .. k0-1 see Y = k delta soft(B) with ||.||_2 <= tau
+        rec = plain.trace[k]
+        assert rec.r_k == 0
+        assert np.allclose(rec.y_omega, k * delta * soft, rtol=0, atol=1e-12 * np.abs(soft).max() * k0 * delta)
+    for a, b in zip(kicked.trace, plain.trace[k0:]):
+        assert a.r_k == b.r_k
+        assert np.abs(a.x_omega - b.x_omega).max() <= 1e-9 * max(1.0, np.abs(a.x_omega).max())
+
+
+def test_dantzig_limit_satisfies_kkt():
+    """The limit of the Dantzig iteration solves min tau||X||_* + 1/2||X||_F^2 s.t. |B - X| <= E on
+    Omega: feasibility, multipliers Y_+, Y_- >= 0 with complementary slackness (Y_+ > 0 only where
+    B - X = E, Y_- > 0 only where X - B = E) and stationarity X = D_tau(Y_+ - Y_-)."""
+    p = _ds_problem(8, 7, 2, 40, 7, 0.5)
+    E = 0.3
+    tau = 2.0
+    res = osvt.svt_dantzig(p.n1, p.n2, p.rows, p.cols, p.vals, E, tau, 0.9, eps=1e-11, k_max=20000,
+                           keep_trace=True)
+    assert res.converged
+    x = res.trace[-1].x_omega
+    b = p.vals
+    scale = np.abs(b).max()
+    assert np.all(np.abs(b - x) <= E + 1e-9 * scale)
+    assert np.all(res.yp >= 0) and np.all(res.ym >= 0)
+    ymax = max(res.yp.max(), res.ym.max(), 1.0)
+    act_p = res.yp > 1e-6 * ymax
+    act_m = res.ym > 1e-6 * ymax
+    assert np.all(np.abs((b - x)[act_p] - E) <= 1e-6 * scale)
+    assert np.all(np.abs((x - b)[act_m] - E) <= 1e-6 * scale)
+    # stationarity: X = D_tau(Y_+ - Y_-) (the multipliers of the last step)
+    U, d, V, _ = osvt.shrink(osvt.dense_from_omega(p.n1, p.n2, p.rows, p.cols, res.yp - res.ym), tau)
+    x_st = sample_X(p.rows, p.cols, U * d, V)
+    assert np.abs(x_st - x).max() <= 1e-6 * scale
