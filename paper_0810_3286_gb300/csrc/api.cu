@@ -612,13 +612,16 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
     // theta_s > tau already proves sigma_s > tau: the rank policy grows s without waiting for
     // convergence.  Otherwise every Ritz triplet above tau must be converged to `tol`, and the
-    // first Ritz value at or below tau must be bounded away from it (theta + residual <= tau).
+    // first Ritz value at or below tau must be resolved (residual <= 1e-3 theta_1: the Krylov
+    // space has found the singular value it stands for; an unresolved Ritz value with a large
+    // residual bounds no particular singular value) and bounded away from tau
+    // (theta + residual <= tau).
     const bool grow = !strict && th[s_eff - 1] > tau && s < kmin;
     int conv = 0;
     bool all_conv = !grow;
     for (int i = 0; i < s_eff && all_conv; ++i) {
       const bool above = strict || th[i] > tau;
-      const bool ok = rs[i] <= tol * th[0] || (!above && th[i] + rs[i] <= tau);
+      const bool ok = rs[i] <= tol * th[0] || (!above && rs[i] <= 1e-3 * th[0] && th[i] + rs[i] <= tau);
       if (!ok) all_conv = false;
       else ++conv;
       if (!above) break;
