@@ -56,7 +56,13 @@ typedef enum svt_status {
 /* Arithmetic of the per-nonzero work (Y, M values, the two sparse products, X on Omega and the
  * dual step).  The Lanczos basis, its reorthogonalisation and the projected SVD that fixes the
  * singular values compared against tau are float64 in every mode. */
-enum { SVT_FP64 = 0, SVT_FP32 = 1 };
+enum { SVT_FP64 = 0, SVT_FP32 = 1, SVT_BF16 = 2 };
+/* SVT_BF16: float32 values and dual iterate as SVT_FP32, plus bfloat16 copies of Y (written by the
+ * fused update) that the sparse products read, with float32 accumulation, while the relative
+ * residual of eq. (5.5) is at or above svt_options.bf16_switch; once it falls below, the products
+ * read the float32 values for the rest of the solve.  bfloat16 rounding of Y (8 significant bits)
+ * perturbs the shrink by about 4e-3 |Y_ij| per entry, which stalls the residual well above 1e-4,
+ * hence the switch.  The Dantzig-selector form runs in float32 throughout. */
 
 typedef struct svt_options {
   int precision;          /* SVT_FP64 (default) or SVT_FP32 */
@@ -79,6 +85,8 @@ typedef struct svt_options {
   int restart_steps;      /* block steps J of a cycle that thick-restarts a non-converged one (block 0
                              = the leading Ritz pairs, block 1 = the residual block); 0 = same as
                              lanczos_steps */
+  double bf16_switch;     /* SVT_BF16 only: relative residual below which the sparse products move
+                             from the bfloat16 copies to the float32 values (default 1e-2) */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */

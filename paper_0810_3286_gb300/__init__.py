@@ -17,10 +17,11 @@ from typing import Optional
 import numpy as np
 
 from . import _abi
-from ._abi import (SVT_ERR_NOT_CONVERGED, SVT_FP32, SVT_FP64, SVT_OK, SVT_STOPPED, SVTError, svt_options,
+from ._abi import (SVT_BF16, SVT_ERR_NOT_CONVERGED, SVT_FP32, SVT_FP64, SVT_OK, SVT_STOPPED, SVTError, svt_options,
                    svt_result, svt_step_info)
 
-__all__ = ["Solver", "SVTError", "sample_omega", "library", "SVT_FP64", "SVT_FP32", "StepInfo", "SolveResult"]
+__all__ = ["Solver", "SVTError", "sample_omega", "library", "SVT_FP64", "SVT_FP32", "SVT_BF16", "StepInfo",
+           "SolveResult"]
 
 
 def library():
@@ -71,11 +72,11 @@ class Solver:
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
                  max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
-                 restart_steps: int = 0):
+                 restart_steps: int = 0, bf16_switch: float = 1e-2):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
-        opt.precision = {"fp64": SVT_FP64, "fp32": SVT_FP32}[precision]
+        opt.precision = {"fp64": SVT_FP64, "fp32": SVT_FP32, "bf16": SVT_BF16}[precision]
         opt.ell = ell
         opt.k_max = k_max
         opt.lanczos_steps = lanczos_steps
@@ -86,6 +87,7 @@ class Solver:
         opt.fused_orth = 1 if fused_orth else 0
         opt.block = int(block)
         opt.restart_steps = int(restart_steps)
+        opt.bf16_switch = float(bf16_switch)
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda

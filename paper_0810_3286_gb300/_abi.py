@@ -32,6 +32,7 @@ STATUS_NAMES = {
 
 SVT_FP64 = 0
 SVT_FP32 = 1
+SVT_BF16 = 2
 
 
 class svt_options(ctypes.Structure):
@@ -49,6 +50,7 @@ class svt_options(ctypes.Structure):
         ("stream", ctypes.c_void_p),
         ("fused_orth", ctypes.c_int),
         ("restart_steps", ctypes.c_int),
+        ("bf16_switch", ctypes.c_double),
     ]
 
 

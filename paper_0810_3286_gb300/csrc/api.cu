@@ -61,7 +61,7 @@ struct svt_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   struct ProfNode { int cls; double bytes, flops; cudaEvent_t a, b; };
   struct CycleGraph {
-    int b, J, ycur, twoc, thick, Jprev;
+    int b, J, ycur, twoc, thick, Jprev, bf16;
     unsigned int prof_mask;
     cudaGraphExec_t exec;
     int64_t launches;
@@ -72,6 +72,11 @@ struct svt_ctx {
   int64_t m = 0, n = 0, nnz = 0;
   int prec = SVT_FP64;
   size_t vbytes = 8;
+  // bfloat16 ladder (precision SVT_BF16, float32 values otherwise): bfloat16 copies of Y (row- and
+  // column-major, ping-pong) feed the sparse products while bf16_active
+  bool bf16_mode = false, bf16_active = false;
+  void* Yb[2] = {nullptr, nullptr};
+  void* Ybc[2] = {nullptr, nullptr};
   std::string last_error;
   std::vector<void*> allocations;
 
@@ -444,13 +449,17 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
     double* Uj = c->Ub + j * su;
     double* Vj = c->Vb + j * sv;
     l += prof_launch_f(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), 2.0 * c->nnz * b, [&] {
-      return launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, c->Vsh, Uj, m, b, c->st, c->nnz);
+      return c->bf16_active
+                 ? launch_spmm(2, c->row_ptr, c->col_idx, c->Yb[c->ycur], Vj, c->Vsh, Uj, m, b, c->st, c->nnz)
+                 : launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, c->Vsh, Uj, m, b, c->st, c->nnz);
     });
     TRY(launched(c, l)); l = 0;
     TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b, c->Ush));
     double* Vn = c->Vb + (j + 1) * sv;
     l += prof_launch_f(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b), 2.0 * c->nnz * b, [&] {
-      return launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
+      return c->bf16_active
+                 ? launch_spmm(2, c->col_ptr, c->row_idx, c->Ybc[c->ycur], Uj, c->Ush, Vn, n, b, c->st, c->nnz)
+                 : launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
     });
     TRY(launched(c, l)); l = 0;
     // the float32 copy of the last block V_J is kept for a thick restart
@@ -483,9 +492,10 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
   const int twoc = c->two_corrections ? 1 : 0;
   const int tk = thick ? 1 : 0;
   const int jp = thick ? Jprev : 0;
+  const int bf = c->bf16_active ? 1 : 0;
   for (auto& g : c->graphs)
     if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.thick == tk && g.Jprev == jp &&
-        g.prof_mask == c->prof_mask) {
+        g.bf16 == bf && g.prof_mask == c->prof_mask) {
       CU(c, cudaGraphLaunch(g.exec, c->st));
       c->launches += g.launches;
       // the graph's event-record nodes fire again on every replay: harvest them at the next sync
@@ -524,7 +534,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
     (void)cudaGetLastError();
     return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
   }
-  c->graphs.push_back({b, J, c->ycur, twoc, tk, jp, c->prof_mask, exec, nl, prof});
+  c->graphs.push_back({b, J, c->ycur, twoc, tk, jp, bf, c->prof_mask, exec, nl, prof});
   CU(c, cudaGraphLaunch(exec, c->st));
   c->launches += nl;
   for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.flops, pn.a, pn.b, true});
@@ -722,6 +732,7 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->stream = nullptr;
   opt->fused_orth = 1;
   opt->restart_steps = 0;
+  opt->bf16_switch = 1e-2;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -872,6 +883,12 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Vf, (size_t)n * cap));
   TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
   TRY(dalloc_t(c, &c->Uwarm, (size_t)m * kBMax));
+  if (c->bf16_mode) {
+    for (int i = 0; i < 2; ++i) {
+      TRY(dalloc(c, &c->Yb[i], nnz * 2));
+      TRY(dalloc(c, &c->Ybc[i], nnz * 2));
+    }
+  }
   if (c->prec == SVT_FP32) {
     const size_t capf = (size_t)((cap + 3) & ~3);
     TRY(dalloc_t(c, &c->Ush, (size_t)m * kBMax));
@@ -938,7 +955,9 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   svt_options o;
   svt_default_options(&o);
   if (opt) o = *opt;
-  if (o.precision != SVT_FP64 && o.precision != SVT_FP32) return fail(nullptr, SVT_ERR_ARG, "unknown precision");
+  if (o.precision != SVT_FP64 && o.precision != SVT_FP32 && o.precision != SVT_BF16)
+    return fail(nullptr, SVT_ERR_ARG, "unknown precision");
+  if (o.precision == SVT_BF16 && !(o.bf16_switch >= 0.0)) return fail(nullptr, SVT_ERR_ARG, "bf16_switch must be >= 0");
   if (o.ell < 1) o.ell = 5;
   if (o.k_max < 1) o.k_max = 1000;
   if (o.lanczos_steps < 1) o.lanczos_steps = 3;
@@ -947,7 +966,8 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   if (!c) return fail(nullptr, SVT_ERR_OOM, "host allocation failed");
   c->opt = o;
   c->m = m; c->n = n; c->nnz = nnz;
-  c->prec = o.precision;
+  c->bf16_mode = o.precision == SVT_BF16;
+  c->prec = c->bf16_mode ? SVT_FP32 : o.precision;   // float32 values; the bfloat16 copies are extra
   c->vbytes = c->prec == SVT_FP64 ? 8 : 4;
   c->user_st = (cudaStream_t)o.stream;
   svt_status s = SVT_OK;
@@ -1011,6 +1031,14 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
   else
     TRY(launched(c, launch_scale_values(c->prec, c->Mv, (double)c->k0 * c->delta, c->Ycsr[0], c->Ycsc[0],
                                         c->csr_to_csc, c->nnz, c->st)));
+  c->bf16_active = false;
+  if (c->bf16_mode && !(c->ds_E > 0.0)) {
+    // the kick's ||P_Omega M||_2 above was taken on the float32 values; the iterations start on
+    // the bfloat16 copies
+    TRY(launched(c, launch_to_bf16((const float*)c->Ycsr[0], (const float*)c->Ycsc[0], c->Yb[0], c->Ybc[0], c->nnz,
+                                   c->st)));
+    c->bf16_active = true;
+  }
   c->r = 0;
   c->k = 0;
   c->d_host.clear();
@@ -1055,7 +1083,8 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, upd_bytes, (2.0 * r + 4.0) * c->nnz, [&] {
     return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
                                c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
-                               c->upd_partial, c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr);
+                               c->upd_partial, c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr,
+                               c->bf16_active ? c->Yb[nxt] : nullptr, c->bf16_active ? c->Ybc[nxt] : nullptr);
   })));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaEventRecord(c->ev1, c->st));
@@ -1083,6 +1112,8 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   } else if (res <= c->eps) {
     return SVT_STOPPED;
   }
+  // bfloat16 ladder: from here on the sparse products read the float32 values
+  if (c->bf16_active && res < c->opt.bf16_switch) c->bf16_active = false;
   c->ycur = nxt;
   return SVT_OK;
 }
@@ -1355,7 +1386,7 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   h.magic = kStateMagic; h.m = c->m; h.n = c->n; h.nnz = c->nnz; h.prec = c->prec; h.r = c->r;
   h.warm_cols = c->warm_cols; h.configured = c->configured; h.k0 = c->k0; h.k = c->k; h.tau = c->tau;
   h.delta = c->delta; h.eps = c->eps; h.norm2 = c->norm2; h.max_rank = c->max_rank; h.rng_counter = c->rng_counter;
-  h.flags = c->two_corrections ? 1 : 0;
+  h.flags = (c->two_corrections ? 1 : 0) | (c->bf16_active ? 2 : 0);
   h.noise_sigma = c->noise_sigma; h.noise_eps = c->noise_eps; h.ds_E = c->ds_E;
   char* p = (char*)buf;
   std::memcpy(p, &h, sizeof h); p += sizeof h;
@@ -1389,6 +1420,7 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
   c->tau = h.tau; c->delta = h.delta; c->eps = h.eps; c->norm2 = h.norm2; c->max_rank = h.max_rank;
   c->rng_counter = h.rng_counter;
   c->two_corrections = (h.flags & 1) != 0;
+  if ((h.flags & 2) && !c->bf16_mode) return fail(c, SVT_ERR_ARG, "state of a bfloat16 context");
   if (!std::isfinite(h.ds_E) || !std::isfinite(h.noise_sigma) || !std::isfinite(h.noise_eps))
     return fail(c, SVT_ERR_ARG, "corrupt state");
   if (h.ds_E > 0.0) TRY(svt_set_dantzig(c, h.ds_E));
@@ -1408,6 +1440,7 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
     CU(c, cudaMemcpyAsync(c->Yp[c->ycur], p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st)); p += c->nnz * c->vbytes;
     CU(c, cudaMemcpyAsync(c->Ym[c->ycur], p, c->nnz * c->vbytes, cudaMemcpyHostToDevice, c->st));
   }
+  c->bf16_active = (h.flags & 2) != 0;
   // rebuild the column-major copy of Y from the row-major values
   if (c->prec == SVT_FP64)
     TRY(launched(c, launch_gather_f64((const double*)ycur_csr(c), c->csc_to_csr, c->nnz, (double*)ycur_csc(c), c->st)));
@@ -1419,6 +1452,9 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
     CU(c, cudaStreamSynchronize(c->st));
     c->allocations.pop_back();
     cudaFree(tmp);
+    if (c->bf16_active)
+      TRY(launched(c, launch_to_bf16((const float*)ycur_csr(c), (const float*)ycur_csc(c), c->Yb[c->ycur],
+                                     c->Ybc[c->ycur], c->nnz, c->st)));
   }
   return sync_and_check(c);
 }

@@ -55,7 +55,8 @@ int launch_omega_compact(uint64_t seed, long long N, long long n_cols, const voi
 // ----- per-iteration kernels -------------------------------------------------------------------
 // Out (n_out x b, float64) = S X with S given in compressed segments (ptr, idx, val) and X (n_in x b).
 // precision 0: float64 values, X and accumulation; 1: float32 values and accumulation, X read from
-// the float32 copy Xf when given (b a multiple of 4), else from the float64 X.
+// the float32 copy Xf when given (b a multiple of 4), else from the float64 X; 2: bfloat16 values,
+// float32 copy Xf (required) and float32 accumulation.
 // nnz (the total segment length) chooses how many warps share a segment.
 int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
                 const float* Xf, double* Out, int n_out, int b, cudaStream_t st, long long nnz);
@@ -129,6 +130,8 @@ int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStre
 //   y_out_csc[csr_to_csc[p]] = y_out[p] (if y_out_csc);  res2 = sum e^2 (deterministic).
 // Factors: float64 Ut (m x r) and V (n x r), or, for precision 1 when Utf and Vf32 are given,
 // float32 copies with leading dimension ldf (a multiple of 4, >= r).
+// ys_out / ys_out_csc (both or neither; float32 values only): bfloat16 copies of y_out and of its
+// column-major copy (y_out_csc required).
 // dual (may be NULL): the two-multiplier form of the matrix Dantzig selector (iteration (iterDS2)):
 //   yp_out = [yp_in + delta (e - E)]_+, ym_out = [ym_in + delta (-e - E)]_+, y_out = yp_out - ym_out,
 //   res2 = sum [|e| - E]_+^2; y_in is unused.  Needs the float32 factor copies when precision is 1.
@@ -143,7 +146,9 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
                         double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
-                        const SddmmDual* dual = nullptr);
+                        const SddmmDual* dual = nullptr, void* ys_out = nullptr, void* ys_out_csc = nullptr);
+// bfloat16 copies (round to nearest) of the float32 values y (row-major) and y_csc.
+int launch_to_bf16(const float* y, const float* y_csc, void* yb, void* yb_csc, long long nnz, cudaStream_t st);
 // y = alpha soft_E(B) (plus the column-major copy), yp = alpha [B - E]_+, ym = alpha [-B - E]_+
 // (any of y_csc, yp, ym may be NULL).
 int launch_dual_kick(int precision, const void* B, double alpha, double E, void* y, void* y_csc, void* yp, void* ym,

@@ -1,6 +1,8 @@
 // Per-iteration kernels that stream Omega: the two sparse products of the Lanczos partial SVD
 // (Y V and Y^T U, Sec. 2.2 / Sec. 5.1.1) and the fused X-on-Omega + dual step + residual of
 // Algorithm 1 (Sec. 5.1.5; residual of eq. (5.5)).
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -144,6 +146,11 @@ static void spmm_launch(const int32_t* ptr, const int32_t* idx, const VT* val, c
 int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
                 const float* Xf, double* Out, int n_out, int b, cudaStream_t st, long long nnz) {
   if (n_out <= 0) return 0;
+  if (precision == 2) {
+    if (!Xf) return 0;   // bfloat16 values are read only with the float32 copy of the dense block
+    spmm_launch<__nv_bfloat16, float, float>(ptr, idx, (const __nv_bfloat16*)val, Xf, Out, n_out, b, st, nnz);
+    return 1;
+  }
   if (precision == 0)
     spmm_launch<double, double, double>(ptr, idx, (const double*)val, X, Out, n_out, b, st, nnz);
   else if (Xf)
@@ -190,7 +197,8 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
                const int32_t* __restrict__ csr_to_csc, const VT* __restrict__ M, const VT* __restrict__ y_in,
                VT* __restrict__ y_out, VT* __restrict__ y_out_csc, const FT* __restrict__ Ut,
                const FT* __restrict__ V, int r, int ldf, int n_rows, AT delta, double* __restrict__ partial,
-               unsigned int* err, DualArgs<VT> ds) {
+               unsigned int* err, DualArgs<VT> ds, __nv_bfloat16* __restrict__ ys_out,
+               __nv_bfloat16* __restrict__ ys_out_csc) {
   __shared__ double red[UPD_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
@@ -225,7 +233,7 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
       } else {
         yp = live ? (AT)y_in[p] : (AT)0;
       }
-      const int q = (live && y_out_csc) ? csr_to_csc[p] : 0;
+      const int q = (live && (y_out_csc || ys_out)) ? csr_to_csc[p] : 0;
       AT x0 = 0, x1 = 0;
 #pragma unroll
       for (int t = 0; t < RMAX; ++t) {
@@ -245,12 +253,22 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
           const VT yn = (VT)(ypn - ymn);
           y_out[p] = yn;
           if (y_out_csc) y_out_csc[q] = yn;
+          if (ys_out) {
+            const __nv_bfloat16 yb = __float2bfloat16_rn((float)yn);
+            ys_out[p] = yb;
+            ys_out_csc[q] = yb;
+          }
           const AT v = fmax(fabs(ev) - E, (AT)0);
           acc += v * v;
         } else {
           VT yn = (VT)(yp + delta * ev);
           y_out[p] = yn;
           if (y_out_csc) y_out_csc[q] = yn;
+          if (ys_out) {
+            const __nv_bfloat16 yb = __float2bfloat16_rn((float)yn);
+            ys_out[p] = yb;
+            ys_out_csc[q] = yb;
+          }
           acc += ev * ev;
         }
       }
@@ -289,23 +307,26 @@ template <typename VT, typename AT, typename FT, bool DS>
 static void sddmm_dispatch(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc, const VT* M,
                            const VT* y_in, VT* y_out, VT* y_out_csc, const FT* Ut, const FT* V, int r, int ldf,
                            int n_rows, AT delta, int blocks, double* partial, unsigned int* err, cudaStream_t st,
-                           DualArgs<VT> ds) {
+                           DualArgs<VT> ds, __nv_bfloat16* ys = nullptr, __nv_bfloat16* ys_csc = nullptr) {
   if (r <= 16)
     k_sddmm_update<VT, AT, FT, 16, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
   else if (r <= 32)
     k_sddmm_update<VT, AT, FT, 32, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
   else
     k_sddmm_update<VT, AT, FT, 64, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
 }
 
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
                         double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
-                        const SddmmDual* dual) {
+                        const SddmmDual* dual, void* ys_out, void* ys_out_csc) {
+  __nv_bfloat16* ys = static_cast<__nv_bfloat16*>(ys_out);
+  __nv_bfloat16* ysc = static_cast<__nv_bfloat16*>(ys_out_csc);
+  if ((ys != nullptr) != (ysc != nullptr) || (ys && !y_out_csc)) return 0;
   if (precision == 0) {
     DualArgs<double> ds{};
     if (dual) {
@@ -324,11 +345,11 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
       ds = {(const float*)dual->yp_in, (const float*)dual->ym_in, (float*)dual->yp_out, (float*)dual->ym_out, dual->E};
       sddmm_dispatch<float, float, float, true>(row_ptr, col_idx, csr_to_csc, (const float*)M, nullptr,
                                                 (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
-                                                (float)delta, UPD_BLOCKS, partial, err, st, ds);
+                                                (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc);
     } else {
       sddmm_dispatch<float, float, float, false>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
                                                  (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
-                                                 (float)delta, UPD_BLOCKS, partial, err, st, ds);
+                                                 (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc);
     }
   } else {
     if (dual) return 0;   // the two-multiplier form runs only with the float32 copies of the factors
@@ -362,6 +383,22 @@ int launch_scale_values(int precision, const void* M, double alpha, void* y, voi
     k_scale_values<double><<<blocks, 256, 0, st>>>((const double*)M, alpha, (double*)y, (double*)y_csc, csr_to_csc, nnz);
   else
     k_scale_values<float><<<blocks, 256, 0, st>>>((const float*)M, alpha, (float*)y, (float*)y_csc, csr_to_csc, nnz);
+  return 1;
+}
+
+// bfloat16 copies (round to nearest) of float32 values, row-major and column-major order.
+__global__ void k_to_bf16(const float* __restrict__ y, const float* __restrict__ y_csc, __nv_bfloat16* __restrict__ yb,
+                          __nv_bfloat16* __restrict__ yb_csc, long long nnz) {
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (long long)gridDim.x * blockDim.x) {
+    yb[p] = __float2bfloat16_rn(y[p]);
+    yb_csc[p] = __float2bfloat16_rn(y_csc[p]);
+  }
+}
+
+int launch_to_bf16(const float* y, const float* y_csc, void* yb, void* yb_csc, long long nnz, cudaStream_t st) {
+  int blocks = (int)svt_min_ll(svt_ceil_div(nnz, 256), 152LL * 16);
+  if (blocks < 1) return 0;
+  k_to_bf16<<<blocks, 256, 0, st>>>(y, y_csc, (__nv_bfloat16*)yb, (__nv_bfloat16*)yb_csc, nnz);
   return 1;
 }
 
@@ -442,7 +479,8 @@ int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, con
                              double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
                              int blocks, double* partial, double* res2, cudaStream_t st) {
   sddmm_dispatch<double, double, double, false>(row_ptr, col_idx, nullptr, M, y_in, y_out, nullptr, Ut, V, r, r,
-                                                n_rows, delta, blocks, partial, nullptr, st, DualArgs<double>{});
+                                                n_rows, delta, blocks, partial, nullptr, st, DualArgs<double>{}, nullptr,
+                                                nullptr);
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, blocks, res2);
   return 2;
 }

@@ -4,6 +4,8 @@
   oracle iterate by iterate (X^k on Omega within 1e-5, identical ranks, same k0 and iteration
   count); the float32 path within 1e-3 per iterate and +-2 iterations; the recovered matrices
   agree to 1e-3 (||X_gpu - X_orc||_F / ||X_orc||_F in closed form from the factors).
+* bfloat16 values (SVT_BF16 ladder) on the companion against the float64 oracle, and at 10000^2
+  against the float32 path.
 * Full-size workloads 10000^2 and 30000^2 (sampled outputs): after 25 float32 iterations the GPU's
   own dual iterate Y is shrunk by the library (svt_shrink) and by the oracle; the singular values
   above tau agree to 1e-5 relative and X on 20,000 sampled entries of Omega to 1e-4 relative.
@@ -95,3 +97,58 @@ def test_full_size_shrink_sampled(cuda, name, seed):
     x_gpu = sample_X(rows[pick], ci[pick], U * d, V)
     x_orc = sample_X(rows[pick], ci[pick], Uo * do, Vo)
     assert np.linalg.norm(x_gpu - x_orc) <= 1e-4 * np.linalg.norm(x_orc)
+
+
+def test_companion_2000_bf16_ladder(cuda, companion_run):
+    """bfloat16 values (SVT_BF16, switching to float32 below a relative residual of 1e-2) against the
+    float64 oracle: per-iterate error within 4e-3 (bfloat16 keeps 8 significant bits, unit roundoff
+    2^-9 ~ 2e-3 per value of Y, a perturbation of the shrink of the same relative size), within 1e-3
+    once the products read float32 values, the stopping iteration within 2 and the recovered
+    matrices within 1e-3."""
+    torch = cuda
+    from paper_0810_3286_gb300 import Solver
+    p, ref = companion_run
+    s = Solver(p.n1, p.n2, torch.from_numpy(p.rows).cuda(), torch.from_numpy(p.cols).cuda(),
+               torch.from_numpy(p.vals).cuda(), precision="bf16", bf16_switch=1e-2)
+    s.configure(p.tau_default(), p.delta_default(), 1e-4, 27, ref.k0)
+    stopped, switched = None, False
+    for rec in ref.trace:
+        info = s.step()
+        U, d, V = s.factors()
+        err = _guarded(sample_X(p.rows, p.cols, U * d, V), rec.x_omega, p.vals)
+        assert err <= (1e-3 if switched else 4e-3), (info["k"], err)
+        switched = switched or info["residual"] < 1e-2
+        if info["stopped"]:
+            stopped = info["k"]
+            break
+    extra = 0
+    while stopped is None and extra < 2:
+        info = s.step()
+        extra += 1
+        if info["stopped"]:
+            stopped = info["k"]
+    assert stopped is not None and abs(stopped - ref.iters) <= 2
+    U, d, V = s.factors()
+    assert _x_frob_diff(U, d, V, ref.U, ref.d, ref.V) <= 1e-3
+    s.close()
+
+
+def test_bf16_ladder_10000(cuda):
+    """The 10000^2 rank-10 workload with bfloat16 values: converges to eps = 1e-4 with the planted rank,
+    relative error < 2e-4 and within two iterations of the float32 path."""
+    torch = cuda
+    from paper_0810_3286_gb300 import Solver
+    p = config_problem("single_10000", 0)
+    args = (p.n1, p.n2, torch.from_numpy(p.rows).cuda(), torch.from_numpy(p.cols).cuda(), torch.from_numpy(p.vals).cuda())
+    out = {}
+    for prec in ("fp32", "bf16"):
+        with Solver(*args, precision=prec) as s:
+            res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27)
+            U, d, V = s.factors()
+            A, B = p.A, p.B
+            nx2 = float(np.sum(d * d))
+            nm2 = float(np.trace((A.T @ A) @ (B.T @ B)))
+            xm = float(np.trace(np.diag(d) @ (U.T @ A) @ (B.T @ V)))
+            out[prec] = (res["iterations"], res["rank"], math.sqrt(max(nx2 - 2 * xm + nm2, 0.0) / nm2))
+    assert out["bf16"][1] == 10 and out["bf16"][2] < 2e-4
+    assert abs(out["bf16"][0] - out["fp32"][0]) <= 2, out
