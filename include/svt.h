@@ -136,6 +136,14 @@ void svt_default_options(svt_options* opt);
 svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_t* rows, const int32_t* cols,
                       const double* M_omega, const svt_options* opt, svt_ctx** out);
 
+/*
+ * Upper estimate of the device memory a context of this size takes (its persistent buffers, the
+ * peak scratch of the structure build in svt_create, and a fixed allowance), for admission
+ * control by memory.  Host-only: touches no device.  0 for invalid sizes.  A Dantzig-selector
+ * context (svt_set_dantzig) needs 4 nnz value-bytes more.
+ */
+size_t svt_estimate_device_bytes(int64_t m, int64_t n, int64_t nnz, const svt_options* opt);
+
 /* Releases all device and host memory of the context.  NULL is ignored. */
 void svt_destroy(svt_ctx* ctx);
 
@@ -314,7 +322,8 @@ svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* 
  * Cumulative solver counters since svt_create, written to out[0 .. min(n, 8)):
  *   [0] Lanczos cycles, [1] sparse products, [2] projected-SVD calls, [3] Jacobi sweeps in them,
  *   [4] basis columns deflated as numerically dependent, [5] largest orthonormality defect
- *   max |P^T P - I| seen after the Cholesky pass, [6] kernel launches, [7] reserved (0).
+ *   max |P^T P - I| seen after the Cholesky pass, [6] kernel launches, [7] shrinks whose Lanczos
+ *   stagnated and were accepted at a relaxed tolerance (30x after 10 cycles, 300x after 25).
  * Synchronises the stream.
  */
 svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);

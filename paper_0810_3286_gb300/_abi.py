@@ -89,6 +89,64 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _ctxp = ctypes.c_void_p
 
 # name -> (restype, argtypes)
+class svt_server_options(ctypes.Structure):
+    _fields_ = [
+        ("slots", ctypes.c_int),
+        ("device_budget", ctypes.c_size_t),
+        ("keep_factors", ctypes.c_int),
+        ("dry_run", ctypes.c_int),
+    ]
+
+
+class svt_job(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64),
+        ("n", ctypes.c_int64),
+        ("nnz", ctypes.c_int64),
+        ("rows", ctypes.c_void_p),
+        ("cols", ctypes.c_void_p),
+        ("vals", ctypes.c_void_p),
+        ("tau", ctypes.c_double),
+        ("delta", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("max_rank", ctypes.c_int),
+        ("noise_sigma", ctypes.c_double),
+        ("noise_eps", ctypes.c_double),
+        ("opt", svt_options),
+        ("dry_run_us", ctypes.c_int64),
+        ("dry_run_bytes", ctypes.c_size_t),
+    ]
+
+
+class svt_job_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iterations", ctypes.c_int64),
+        ("rank", ctypes.c_int),
+        ("residual", ctypes.c_double),
+        ("t_submit_ms", ctypes.c_double),
+        ("t_start_ms", ctypes.c_double),
+        ("t_end_ms", ctypes.c_double),
+        ("device_bytes", ctypes.c_size_t),
+    ]
+
+
+class svt_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64),
+        ("completed", ctypes.c_int64),
+        ("failed", ctypes.c_int64),
+        ("queued", ctypes.c_int64),
+        ("running", ctypes.c_int64),
+        ("p50_ms", ctypes.c_double),
+        ("p99_ms", ctypes.c_double),
+        ("mean_ms", ctypes.c_double),
+        ("solves_per_s", ctypes.c_double),
+        ("peak_bytes", ctypes.c_size_t),
+        ("peak_running", ctypes.c_int),
+    ]
+
+
 PROTOTYPES = {
     "svt_default_options": (None, [ctypes.POINTER(svt_options)]),
     "svt_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp,
@@ -115,6 +173,16 @@ PROTOTYPES = {
     "svt_load_state": (ctypes.c_int, [_ctxp, _vp, ctypes.c_size_t]),
     "svt_kernel_launches": (ctypes.c_int64, [_ctxp]),
     "svt_set_profile": (ctypes.c_int, [_ctxp, ctypes.c_uint]),
+    "svt_estimate_device_bytes": (ctypes.c_size_t, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                                    ctypes.POINTER(svt_options)]),
+    "svt_server_default_options": (None, [ctypes.POINTER(svt_server_options)]),
+    "svt_server_create": (ctypes.c_int, [ctypes.POINTER(svt_server_options), ctypes.POINTER(ctypes.c_void_p)]),
+    "svt_server_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(svt_job), ctypes.POINTER(ctypes.c_int64)]),
+    "svt_server_wait": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(svt_job_result), _vp, _vp, _vp,
+                                       ctypes.c_int]),
+    "svt_server_drain": (ctypes.c_int, [ctypes.c_void_p]),
+    "svt_server_stats_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(svt_server_stats)]),
+    "svt_server_destroy": (None, [ctypes.c_void_p]),
     "svt_set_dantzig": (ctypes.c_int, [_ctxp, ctypes.c_double]),
     "svt_set_noise_stop": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.c_double]),
     "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, _vp]),
@@ -125,7 +193,7 @@ PROTOTYPES = {
 }
 
 COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "deflated_columns",
-                 "max_orth_defect", "kernel_launches", "reserved"]
+                 "max_orth_defect", "kernel_launches", "relaxed_shrinks"]
 
 # kernel classes of svt_set_profile / svt_get_profile
 PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update", "orth"]

@@ -15,9 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsvt.so")
-SOURCES = ["omega.cu", "sparse.cu", "dense.cu", "orth.cu", "jacobi.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["omega.cu", "sparse.cu", "dense.cu", "orth.cu", "jacobi.cu", "api.cu", "noalloc.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr"]
 
 
 def nvcc() -> str:
@@ -34,6 +34,7 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(os.path.dirname(HERE), "include", "svt.h"))
+    files.append(os.path.join(os.path.dirname(HERE), "include", "svt_serve.h"))
     return files
 
 
@@ -51,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -66,7 +67,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for obj, err in results:
             print(err)
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp] + [o for o, _ in results]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-Xcompiler", "-pthread", "-o", tmp] + [o for o, _ in results]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

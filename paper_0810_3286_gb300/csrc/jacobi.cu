@@ -19,6 +19,8 @@
 //     Rayleigh quotients, exact to second order in the float32 angle error of w.
 // Residual estimates of the Lanczos relation: res_k = || S x_k[last b rows] || with S the b x b
 // upper triangular factor of the last block (Y^T U_J = V T^T + V_{J+1} S E_J^T).
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -414,8 +416,10 @@ bool jacobi_attrs();
 int init_jacobi_attributes() { return jacobi_attrs() ? 0 : 1; }
 
 bool jacobi_attrs() {
-  static int state = 0;  // 0 unset, 1 ok, 2 failed
-  if (state == 0) {
+  // once per process (contexts may be created from several threads)
+  static std::once_flag once;
+  static int state = 0;  // 1 ok, 2 failed
+  std::call_once(once, [] {
     const size_t mx64 =
         (size_t)(2 * JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
     const size_t mxm = (size_t)(JMAXK * JMAXK + 2 * JMAXB * JMAXK) * sizeof(double) +
@@ -426,7 +430,7 @@ bool jacobi_attrs() {
     set_smem_attrs<9>(mx64, mxm);
     set_smem_attrs<12>(mx64, mxm);
     state = cudaGetLastError() == cudaSuccess ? 1 : 2;
-  }
+  });
   return state == 1;
 }
 

@@ -18,6 +18,7 @@
 // The coefficients satisfy P_in = Q (C1 + C2) + P_out R2 R1 exactly for the factors used; C1 + C2
 // and R2 R1 are the entries of the projected block bidiagonal matrix.
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -549,25 +550,26 @@ static int orth_coop_blocks_per_sm() {
 // Largest co-resident grid of the cooperative kernel for every block size (the same bound is
 // used for all, the smallest of them), capped at two CTAs per SM.  0 if unavailable.
 int orth_coop_init() {
-  static int grid = -1;
-  if (grid >= 0) return grid;
-  int dev = 0, sms = 0, coop = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
-    (void)cudaGetLastError();
-    grid = 0;
-    return grid;
-  }
-  if (!orth_coop_attr<8>() || !orth_coop_attr<16>() || !orth_coop_attr<24>() || !orth_coop_attr<32>()) {
-    (void)cudaGetLastError();
-    grid = 0;
-    return grid;
-  }
-  int bps = std::min(std::min(orth_coop_blocks_per_sm<8>(), orth_coop_blocks_per_sm<16>()),
-                     std::min(orth_coop_blocks_per_sm<24>(), orth_coop_blocks_per_sm<32>()));
-  bps = std::min(bps, 2);
-  grid = bps * sms;
+  // once per process (contexts may be created from several threads)
+  static std::once_flag once;
+  static int grid = 0;
+  std::call_once(once, [] {
+    int dev = 0, sms = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+      (void)cudaGetLastError();
+      return;
+    }
+    if (!orth_coop_attr<8>() || !orth_coop_attr<16>() || !orth_coop_attr<24>() || !orth_coop_attr<32>()) {
+      (void)cudaGetLastError();
+      return;
+    }
+    int bps = std::min(std::min(orth_coop_blocks_per_sm<8>(), orth_coop_blocks_per_sm<16>()),
+                       std::min(orth_coop_blocks_per_sm<24>(), orth_coop_blocks_per_sm<32>()));
+    bps = std::min(bps, 2);
+    grid = bps * sms;
+  });
   return grid;
 }
 

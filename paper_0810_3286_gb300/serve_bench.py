@@ -1,0 +1,112 @@
+"""Serving measurement: a stream of completion jobs through the serving runtime.
+
+    python -m paper_0810_3286_gb300.serve_bench [--jobs 100] [--slots 8] [--load 0.8] [--single 8]
+
+Jobs follow the serving workload: m, n uniform in [500, 8000], rank uniform in 5..20,
+|Omega| = c r (m + n - r) with c uniform in [4, 6], N(0,1) planted factors, eps = 1e-4,
+tau = 5 sqrt(m n), delta = 1.2 m n / |Omega|.  Three measurements on the same jobs:
+  * saturated: all jobs submitted at once; mu = completed jobs per second;
+  * Poisson: arrivals at load x mu (exponential gaps), time to eps of every job measured from its
+    arrival, p50 / p99 by nearest rank;
+  * one job at a time (slots = 1) in float32 and in float64 on the first `--single` jobs: mean time
+    to eps per job, the plain single-job baseline.
+Every job is capped at K_MAX = 500 SVT iterations; jobs that end without meeting the stopping rule
+(iteration cap, more than 27 singular values above tau, Lanczos stagnation) are counted as failed
+and left out of the latency percentiles.  Prints one JSON line.  Problem generation happens before
+any timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+K_MAX = 500
+
+
+def _submit(srv, p, precision):
+    return srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 27,
+                      precision=precision, k_max=K_MAX)
+
+
+def _closed_loop(jobs, slots, precision):
+    from paper_0810_3286_gb300.serve import Server
+    with Server(slots=slots) as srv:
+        ids = [_submit(srv, p, precision) for p in jobs]
+        srv.drain()
+        st = srv.stats()
+        res = [srv.wait(i) for i in ids]
+    return st, res
+
+
+def run(n_jobs=100, slots=8, load=0.8, n_single=8, seed=0):
+    from paper_0810_3286_gb300.serve import Server
+    from svt_inputs import serving_job
+    jobs = [serving_job(seed * 1_000_003 + i) for i in range(n_jobs)]
+    nnz_mean = float(np.mean([p.nnz for p in jobs]))
+    # warm-up: library load, first contexts
+    _closed_loop(jobs[:2], 2, "fp32")
+    sat, res = _closed_loop(jobs, slots, "fp32")
+    mu = sat["solves_per_s"]
+    failed = sum(1 for r in res if r["status"] != 0)
+    # Poisson arrivals at load * mu
+    rng = np.random.default_rng(np.random.PCG64(seed + 17))
+    gaps = rng.exponential(1.0 / (load * mu), size=n_jobs)
+    with Server(slots=slots) as srv:
+        ids = []
+        t_next = time.perf_counter()
+        for p, g in zip(jobs, gaps):
+            t_next += g
+            dt = t_next - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            ids.append(_submit(srv, p, "fp32"))
+        srv.drain()
+        poi = srv.stats()
+        for i in ids:
+            srv.wait(i)
+    single = {}
+    for prec in ("fp32", "fp64"):
+        st, r = _closed_loop(jobs[:n_single], 1, prec)
+        ok = [x for x in r if x["status"] == 0]
+        single[prec] = {"jobs": n_single, "converged": len(ok),
+                        "mean_time_to_eps_ms": float(np.mean([x["t_end_ms"] - x["t_start_ms"] for x in ok])) if ok else None,
+                        "solves_per_s": st["solves_per_s"]}
+    return {
+        "workload": "%d jobs: m, n ~ U[500, 8000], rank ~ U{5..20}, |Omega| = c r (m + n - r), c ~ U[4, 6], "
+                    "mean |Omega| %.0f, eps 1e-4, at most %d iterations, float32" % (n_jobs, nnz_mean, K_MAX),
+        "slots": slots,
+        "saturated": {"solves_per_s": mu, "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
+                      "peak_jobs_in_flight": sat["peak_running"], "peak_device_bytes": sat["peak_bytes"],
+                      "failed": failed},
+        "poisson": {"load": load, "arrival_rate_per_s": load * mu, "solves_per_s": poi["solves_per_s"],
+                    "p50_ms": poi["p50_ms"], "p99_ms": poi["p99_ms"], "mean_ms": poi["mean_ms"],
+                    "completed": poi["completed"], "failed": poi["failed"]},
+        "one_job_at_a_time": single,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--jobs", type=int, default=100)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--single", type=int, default=8)
+    ap.add_argument("--seed", type=int, default=0)
+    args = ap.parse_args()
+    from paper_0810_3286_gb300 import build
+    build.build()
+    print(json.dumps(run(args.jobs, args.slots, args.load, args.single, args.seed)))
+
+
+if __name__ == "__main__":
+    main()

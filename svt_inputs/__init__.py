@@ -10,7 +10,7 @@ Everything is drawn from numpy's PCG64 generator seeded with the caller's seed, 
 (n1, n2, r, m, seed) always yields bit-identical arrays on any host.
 """
 from .planted import (PlantedProblem, planted_problem, config_problem, CONFIGS, dof, sample_count,
-                      random_dense, random_sparse_pattern)
+                      random_dense, random_sparse_pattern, serving_job)
 
 __all__ = ["PlantedProblem", "planted_problem", "config_problem", "CONFIGS", "dof", "sample_count",
-           "random_dense", "random_sparse_pattern"]
+           "random_dense", "random_sparse_pattern", "serving_job"]

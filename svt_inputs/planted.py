@@ -144,3 +144,35 @@ def random_sparse_pattern(n1: int, n2: int, m: int, seed: int, empty_rows=(), em
     cols = (ids % n2).astype(np.int32)
     vals = rng.standard_normal(ids.size)
     return rows, cols, vals
+
+
+def serving_job(seed: int, n_range=(500, 8000), rank_range=(5, 20), c_range=(4.0, 6.0),
+                noise_sigma: float = 0.0) -> PlantedProblem:
+    """One job of the serving workload: m, n uniform in n_range, rank uniform in rank_range,
+    |Omega| = c r (m + n - r) with c uniform in c_range, N(0,1) planted factors, Omega uniform
+    without replacement.  Omega is drawn as the distinct values of i.i.d. uniform ids, a uniform
+    random subset of the right size of them kept (a procedure symmetric in the ids, hence uniform
+    over m-subsets), which is much faster than choice without replacement for large n1 n2."""
+    rng = np.random.default_rng(np.random.PCG64([seed, 0x5E4E]))
+    n1 = int(rng.integers(n_range[0], n_range[1] + 1))
+    n2 = int(rng.integers(n_range[0], n_range[1] + 1))
+    r = int(rng.integers(rank_range[0], rank_range[1] + 1))
+    c = float(rng.uniform(c_range[0], c_range[1]))
+    m = min(int(round(c * r * (n1 + n2 - r))), n1 * n2)
+    A = rng.standard_normal((n1, r))
+    B = rng.standard_normal((n2, r))
+    N = n1 * n2
+    ids = np.zeros(0, dtype=np.int64)
+    draw = m + m // 8 + 64
+    while ids.size < m:
+        ids = np.sort(np.concatenate([ids, rng.integers(0, N, size=draw, dtype=np.int64)]))
+        ids = ids[np.concatenate(([True], ids[1:] != ids[:-1]))]
+    if ids.size > m:
+        ids = np.sort(rng.choice(ids, size=m, replace=False))
+    rows = (ids // n2).astype(np.int32)
+    cols = (ids % n2).astype(np.int32)
+    vals = np.einsum("pt,pt->p", A[rows], B[cols])
+    if noise_sigma > 0.0:
+        vals = vals + noise_sigma * rng.standard_normal(m)
+    return PlantedProblem(n1=n1, n2=n2, r=r, seed=seed, A=A, B=B, rows=rows, cols=cols, vals=vals,
+                          noise_sigma=noise_sigma)

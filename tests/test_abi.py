@@ -1,5 +1,6 @@
-"""The C-ABI library loads and exports every entry point that include/svt.h declares (no GPU
-work: nothing here launches a kernel).  Also checks the binding's prototypes cover the header."""
+"""The C-ABI library loads and exports every entry point that include/svt.h and include/svt_serve.h
+declare (no GPU work: nothing here launches a kernel).  Also checks the binding's prototypes cover
+the headers."""
 import os
 import re
 import subprocess
@@ -7,13 +8,16 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "svt.h")
+HEADERS = [os.path.join(ROOT, "include", "svt.h"), os.path.join(ROOT, "include", "svt_serve.h")]
 
 
 def _declared():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(svt_[a-z_A-Z0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(svt_[a-z_A-Z0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")

@@ -1,0 +1,77 @@
+"""Serving runtime on the GPU: jobs admitted by slots and memory, overlapping on the device.
+
+* Every job's result in a mix of concurrent jobs is the one it gives alone (same status,
+  iterations, rank, residual and factors, bit for bit: the same kernels, launch shapes and
+  fixed-order reductions run in both cases), in float32 and float64.
+* With a budget of 2.5 times the largest job's footprint, the footprints in flight never exceed
+  it, several jobs are in flight at once, and the jobs finish.
+"""
+import numpy as np
+import pytest
+
+from svt_inputs import serving_job
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_jobs(k, seed0):
+    # the better-conditioned end of the serving distribution (oversampling 5.5 - 6): SVT with
+    # tau = 5 sqrt(m n) and delta = 1.2 / p converges on these within k_max
+    return [serving_job(seed0 + i, n_range=(500, 1200), rank_range=(8, 12), c_range=(5.5, 6.0)) for i in range(k)]
+
+
+def _alone(p, precision):
+    from paper_0810_3286_gb300 import Solver
+    from paper_0810_3286_gb300._abi import SVTError
+    with Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision) as s:
+        try:
+            res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27, raise_on_nonconvergence=False)
+            return (0 if res["converged"] else 6), res, s.factors()
+        except SVTError as ex:
+            return ex.status, None, None
+
+
+@pytest.mark.parametrize("precision,k", [("fp32", 8), ("fp64", 3)])
+def test_results_same_alone_and_in_mix(cuda, precision, k):
+    from paper_0810_3286_gb300.serve import Server
+    jobs = _small_jobs(k, 500)
+    if precision == "fp64":
+        jobs = [serving_job(900 + i, n_range=(150, 300), rank_range=(3, 6), c_range=(5.5, 6.0)) for i in range(k)]
+    alone = [_alone(p, precision) for p in jobs]
+    with Server(slots=4, keep_factors=True) as srv:
+        ids = [srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 27,
+                          precision=precision) for p in jobs]
+        mixed = [srv.wait(i) for i in ids]
+        st = srv.stats()
+    assert st["completed"] + st["failed"] == k
+    assert sum(1 for a in alone if a[0] == 0) >= k - 1       # the jobs are meant to converge
+    for (status, res, fac), m in zip(alone, mixed):
+        assert m["status"] == status
+        if res is None:
+            continue
+        U, d, V = fac
+        assert m["iterations"] == res["iterations"] and m["rank"] == res["rank"]
+        assert m["residual"] == res["residual"]
+        assert np.array_equal(m["d"], d) and np.array_equal(m["U"], U) and np.array_equal(m["V"], V)
+
+
+def test_memory_budget_and_overlap(cuda):
+    import ctypes
+    from paper_0810_3286_gb300 import library, _abi
+    from paper_0810_3286_gb300.serve import Server
+    L = library()
+    jobs = _small_jobs(12, 700)
+    o = _abi.svt_options()
+    L.svt_default_options(ctypes.byref(o))
+    o.precision = _abi.SVT_FP32
+    biggest = max(L.svt_estimate_device_bytes(p.n1, p.n2, p.nnz, ctypes.byref(o)) for p in jobs)
+    budget = int(2.5 * biggest)
+    with Server(slots=8, device_budget=budget) as srv:
+        ids = [srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals) for p in jobs]
+        srv.drain()
+        st = srv.stats()
+        res = [srv.wait(i) for i in ids]
+    assert st["completed"] + st["failed"] == 12 and st["completed"] >= 11
+    assert st["peak_bytes"] <= budget
+    assert st["peak_running"] >= 2
+    assert all(r["residual"] <= 1e-4 for r in res if r["status"] == 0)
