@@ -170,9 +170,14 @@ int launch_gram(const double* Q, long long q_stride, int nq, const double* P, in
 // C (nq b x b), R (b x b) and dinv (b) in shared memory.  Called by all threads of the CTA.
 __device__ void update_rows(int mode, const double* __restrict__ Q, long long q_stride, int nq,
                             const double* __restrict__ sC, const double* __restrict__ sR,
-                            const double* __restrict__ sD, double* __restrict__ P, int b, int g, int r0, int r1) {
-  const int rows_per_iter = ORTH_T / g;
-  const int rl = threadIdx.x / g, d = threadIdx.x - rl * g;
+                            const double* __restrict__ sD, double* __restrict__ P, int b, int g, int r0, int r1,
+                            int tid0 = 0, int nthr = ORTH_T) {
+  // threads [tid0, tid0 + nthr) take part (mode 0 only may leave warps out: mode 1 shuffles
+  // within row groups); tid0 and nthr are multiples of 32
+  const int tid = threadIdx.x - tid0;
+  if (tid < 0 || tid >= nthr) return;
+  const int rows_per_iter = nthr / g;
+  const int rl = tid / g, d = tid - rl * g;
   const int gbase = (threadIdx.x & 31) & ~(g - 1);
   for (int ib = r0; ib < r1; ib += rows_per_iter) {   // uniform trip count for the whole CTA
     const int i = ib + rl;
@@ -326,11 +331,15 @@ __device__ void correct_coefs(const double* __restrict__ sU, const double* __res
     if (sRout) sRout[e] = v;
   }
   if (counters && threadIdx.x < 32) {
+    // max |E| over the upper triangle (E is symmetric) of the non-deflated columns, from U(E) in
+    // shared memory: E_ij = U_ij above the diagonal, E_ii = 2 U_ii; a deflated column has
+    // G3_ii = 0, i.e. E_ii = -1
     double mx = 0.0;
     for (int e = threadIdx.x; e < b * b; e += 32) {
-      int i = e / b, j = e - i * b;
-      const double gii = __ldcg(G3 + i * b + i), gjj = __ldcg(G3 + j * b + j);
-      if (gii > 0.5 && gjj > 0.5) mx = fmax(mx, fabs(__ldcg(G3 + e) - (i == j ? 1.0 : 0.0)));
+      const int i = e / b, j = e - i * b;
+      if (j < i) continue;
+      const bool live = 2.0 * sU[i * b + i] > -0.5 && 2.0 * sU[j * b + j] > -0.5;
+      if (live) mx = fmax(mx, fabs(i == j ? 2.0 * sU[e] : sU[e]));
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (threadIdx.x == 0) atomicMax(&counters[3], (unsigned long long)__double_as_longlong(mx));
@@ -499,11 +508,17 @@ __global__ void __launch_bounds__(ORTH_T) k_orth_coop(OrthCoopArgs a) {
     reduce_entries(a.partial, nb, B * B, a.G2, nullptr, nullptr, 0, 0, B);
     SVT_BARRIER_OR_RETURN();
   }
-  // R1 = chol(A) in every CTA; P <- (P - Q C2) R1^-1; E = P^T P - I
-  if (threadIdx.x < 32) chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD, blockIdx.x == 0 ? a.counters : nullptr);
-  for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G2 + t);
+  // R1 = chol(A) in every CTA, by warp 0, while warps 1.. project P <- P - Q C2; then
+  // P <- P R1^-1 (forward substitution) by the whole CTA; E = P^T P - I
+  if (threadIdx.x < 32) {
+    chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD, blockIdx.x == 0 ? a.counters : nullptr);
+  } else if (a.nq > 0) {
+    for (int t = threadIdx.x - 32; t < K * B; t += blockDim.x - 32) sC[t] = __ldcg(a.G2 + t);
+    asm volatile("bar.sync 1, %0;" ::"r"(ORTH_T - 32));   // warps 1.. only
+    update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1, 32, ORTH_T - 32);
+  }
   __syncthreads();
-  update_rows(1, a.Q, a.q_stride, a.nq, sC, sR, sD, a.P, B, a.g, r0, r1);
+  update_rows(1, nullptr, 0, 0, nullptr, sR, sD, a.P, B, a.g, r0, r1);
   __syncthreads();
   gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
   SVT_BARRIER_OR_RETURN();
