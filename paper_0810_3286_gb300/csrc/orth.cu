@@ -248,49 +248,83 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
 }
 
 // ------------------------------------------------------------------------------------------------
-// Cholesky with deflation of the b x b block A of G2 (one warp, lane t owns column t; B = compile-
-// time block size so every loop has exact bounds).  Pivots: float32 reciprocal square root refined
-// by one float64 Newton step (relative error ~1e-14; the float32 seed alone would leave errors of
-// 1e-7 times the condition number of the Gram, which reaches 1e3 - 1e4 in Krylov blocks).
+// Cholesky with deflation of the b x b block A of G2 (one warp; B = compile-time block size so
+// every loop has exact bounds).  A float64 operation of one warp occupies the SM sub-partition's
+// float64 pipe for ~64 cycles whatever the number of active lanes, so the factorisation is timed
+// by its count of warp-wide float64 instructions:
+//   * for B <= 16 the warp is split into H = 32 / B lane groups; lane (h, c) = h B + c owns
+//     column c of the rows i = h, h + H, ... (upper triangle), so a rank-1 update of the trailing
+//     block costs ceil(rows / H) instructions instead of one per row;
+//   * the pivot's reciprocal square root is seeded from the double's bits (exponent halved
+//     exactly, 23 mantissa bits to a float32 rsqrt), refined by one Newton step in float64
+//     (relative error ~1e-13, three float64 instructions); deflation is decided by integer
+//     comparison of the bit patterns against 1e-24 times the column's squared norm before the
+//     projections (precomputed for all columns at once).
+// Columns that lost all but 1e-12 of their norm (or whose pivot is not a normal positive double
+// above 2^-1021) are deflated: R's row is zero and 1 / R_jj = 0.
 // ------------------------------------------------------------------------------------------------
+// Reciprocal square root of a normal positive double (biased exponent 2 .. 2046) to ~1e-13.
+__device__ __forceinline__ double rsqrt_pivot(double d) {
+  const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
+  const int E = (int)((hi >> 20) & 0x7FFu);
+  const int p = 1 - (E & 1);                      // unbiased exponent odd: mantissa scaled into [2, 4)
+  const int k = (E - 1023 - p) >> 1;              // d = m 4^k, m in [1, 4)
+  const float m = __int_as_float((int)(((unsigned int)(127 + p) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29)));
+  const unsigned int f = (unsigned int)__float_as_int(rsqrtf(m));   // in (0.5, 1]
+  const int fe = (int)((f >> 23) & 0xFFu);
+  const double y0 = __hiloint2double((int)(((unsigned int)(fe - 127 + 1023 - k) << 20) | ((f & 0x7FFFFFu) >> 3)),
+                                     (int)((f & 7u) << 29));
+  const double h = __hiloint2double((int)(hi - 0x100000u), (int)lo);   // d / 2, exact
+  const double t = h * y0;
+  const double u = fma(-t, y0, 0.5);              // (1 - d y0^2) / 2
+  return fma(y0, u, y0);
+}
+
 // One warp (lanes 0..31 of the calling warp).  G1 / G2 may have been written by other CTAs of the
 // same kernel: they are read through L2.
 template <int B>
 __device__ __forceinline__ void chol_warp(const double* __restrict__ G1, const double* __restrict__ G2, int nq,
                                           double* __restrict__ R, double* __restrict__ dinv,
                                           unsigned long long* __restrict__ counters) {
-  const int t = threadIdx.x & 31;
+  constexpr int H = B <= 16 ? 32 / B : 1;       // lane groups
+  constexpr int NR = (B + H - 1) / H;           // rows per lane
+  const int lane = threadIdx.x & 31;
+  const int h = lane / B, c = lane - h * B;     // for B = 24 lanes 24..31 get h = 1: idle
+  const bool col = h < H;
   const int K = nq * B;
-  double a[B];
+  double a[NR];
 #pragma unroll
-  for (int i = 0; i < B; ++i) a[i] = (t < B && i <= t) ? __ldcg(G2 + (K + i) * B + t) : 0.0;
-  const double ref = (t < B) ? ((G1 && nq > 0) ? __ldcg(G1 + (K + t) * B + t) : __ldcg(G2 + (K + t) * B + t)) : 0.0;
-  double rcol[B];
+  for (int s = 0; s < NR; ++s) {
+    const int i = s * H + h;
+    a[s] = (col && i < B && i <= c) ? __ldcg(G2 + (K + i) * B + c) : 0.0;
+  }
+  const double ref = col ? ((G1 && nq > 0) ? __ldcg(G1 + (K + c) * B + c) : __ldcg(G2 + (K + c) * B + c)) : 0.0;
+  const long long thr = __double_as_longlong(DEFLATE_REL2 * ref);
   int deflated = 0;
 #pragma unroll
   for (int j = 0; j < B; ++j) {
-    const double d = __shfl_sync(0xffffffffu, a[j], j);
-    const double refj = __shfl_sync(0xffffffffu, ref, j);
-    const bool defl = !(d > DEFLATE_REL2 * refj) || !(d > 0.0);
-    double y = 0.0;
-    if (!defl) {
-      const double y0 = (double)rsqrtf((float)d);
-      y = y0 * (1.5 - 0.5 * d * y0 * y0);  // one Newton step: relative error ~1e-14
-    }
-    deflated += defl ? 1 : 0;
-    const double rjt = (t > j) ? a[j] * y : ((t == j) ? d * y : 0.0);
-    rcol[j] = rjt;
-    if (t == j) dinv[j] = y;
+    const int hj = j % H, sj = j / H;
+    const double d = __shfl_sync(0xffffffffu, a[sj], hj * B + j);
+    const long long tj = __shfl_sync(0xffffffffu, thr, j);
+    const long long db = __double_as_longlong(d);
+    const bool ok = db > tj && db >= 0x0020000000000000LL && db < 0x7FF0000000000000LL;
+    const double y = ok ? rsqrt_pivot(d) : 0.0;
+    deflated += ok ? 0 : 1;
+    // row j of R: R_jc = A_jc y, held by the lanes of group hj in slot sj; broadcast per column
+    const double rown = a[sj] * y;
+    double rj = __shfl_sync(0xffffffffu, rown, (hj * B + c) & 31);
+    if (!col || c < j) rj = 0.0;
+    if (h == 0) R[j * B + c] = rj;
+    if (lane == 0) dinv[j] = y;
+    __syncwarp();
+    // trailing update A_ic -= R_ji R_jc for j < i <= c (R_ji read back from R)
 #pragma unroll
-    for (int i = j + 1; i < B; ++i) {
-      const double rji = __shfl_sync(0xffffffffu, rjt, i);
-      if (t >= i) a[i] -= rji * rjt;
+    for (int s = sj; s < NR; ++s) {
+      const int i = s * H + h;
+      if (col && i > j && i <= c) a[s] = fma(-R[j * B + i], rj, a[s]);
     }
   }
-#pragma unroll
-  for (int j = 0; j < B; ++j)
-    if (t < B) R[j * B + t] = (j <= t) ? rcol[j] : 0.0;
-  if (t == 0 && deflated && counters) atomicAdd(&counters[2], (unsigned long long)deflated);
+  if (lane == 0 && deflated && counters) atomicAdd(&counters[2], (unsigned long long)deflated);
 }
 
 template <int B>
@@ -473,7 +507,7 @@ static constexpr size_t orth_coop_smem(int B) {
   } while (0)
 
 template <int B>
-__global__ void __launch_bounds__(ORTH_T) k_orth_coop(OrthCoopArgs a) {
+__global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   extern __shared__ double sm_orth[];
   double* sC = sm_orth;                 // K x B coefficients (C1, then C2)
   double* sR = sC + OB_MAXK * B;        // R1
