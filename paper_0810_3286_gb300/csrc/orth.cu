@@ -179,7 +179,9 @@ __device__ void update_rows(int mode, const double* __restrict__ Q, long long q_
   const int rows_per_iter = nthr / g;
   const int rl = tid / g, d = tid - rl * g;
   const int gbase = (threadIdx.x & 31) & ~(g - 1);
-  for (int ib = r0; ib < r1; ib += rows_per_iter) {   // uniform trip count for the whole CTA
+  const int wrow = (tid & ~31) / g;   // first row of this warp within an iteration
+  for (int ib = r0; ib < r1; ib += rows_per_iter) {
+    if (ib + wrow >= r1) break;      // no row of this warp is left (warp-uniform)
     const int i = ib + rl;
     const bool live = i < r1 && d < b;
     double v = 0.0;
@@ -347,12 +349,11 @@ __device__ __forceinline__ void correct_load_U(const double* __restrict__ G3, in
   }
 }
 
-// (I + U(E)) R1 -> Tdiag / Rout / sRout (any may be NULL); max |E| -> counters[3].  All threads of
-// one CTA; sU, sR1 in shared memory.
+// (I + U(E)) R1 -> Tdiag / Rout / sRout (any may be NULL).  All threads of one CTA; sU, sR1 in
+// shared memory.
 __device__ void correct_coefs(const double* __restrict__ sU, const double* __restrict__ sR1, int b,
                               double* __restrict__ Tdiag, int ldT, double* __restrict__ Rout,
-                              double* __restrict__ sRout, const double* __restrict__ G3,
-                              unsigned long long* __restrict__ counters) {
+                              double* __restrict__ sRout) {
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     int i = e / b, j = e - i * b;
     double v = 0.0;
@@ -364,30 +365,49 @@ __device__ void correct_coefs(const double* __restrict__ sU, const double* __res
     if (Rout) Rout[e] = v;
     if (sRout) sRout[e] = v;
   }
-  if (counters && threadIdx.x < 32) {
-    // max |E| over the upper triangle (E is symmetric) of the non-deflated columns, from U(E) in
-    // shared memory: E_ij = U_ij above the diagonal, E_ii = 2 U_ii; a deflated column has
-    // G3_ii = 0, i.e. E_ii = -1
-    double mx = 0.0;
-    for (int e = threadIdx.x; e < b * b; e += 32) {
-      const int i = e / b, j = e - i * b;
-      if (j < i) continue;
-      const bool live = 2.0 * sU[i * b + i] > -0.5 && 2.0 * sU[j * b + j] > -0.5;
-      if (live) mx = fmax(mx, fabs(i == j ? 2.0 * sU[e] : sU[e]));
+}
+
+// max |E| over the non-deflated columns -> counters[3] (as the bits of a non-negative double, so
+// atomicMax orders them), from U(E) in shared memory: E_ij = U_ij above the diagonal, E_ii =
+// 2 U_ii; a deflated column has G3_ii = 0, i.e. U_ii = -1/2, and a column counts as live when
+// U_ii > -1/4.  Integer operations on the bit patterns (the float64 pipe is the scarce one); NaN
+// entries are ignored.  One warp (all 32 lanes).
+__device__ void correct_defect(const double* __restrict__ sU, int b, unsigned long long* __restrict__ counters) {
+  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL, kInf = 0x7FF0000000000000LL, kQuarter = 0x3FD0000000000000LL;
+  const int lane = threadIdx.x & 31;
+  long long off = 0, dia = 0;
+  for (int e = lane; e < b * b; e += 32) {
+    const int i = e / b, j = e - i * b;
+    if (j < i) continue;
+    const long long xi = __double_as_longlong(sU[i * b + i]), xj = __double_as_longlong(sU[j * b + j]);
+    const bool li = (xi >= 0 && xi <= kInf) || (xi & kAbs) < kQuarter;
+    const bool lj = (xj >= 0 && xj <= kInf) || (xj & kAbs) < kQuarter;
+    const long long x = __double_as_longlong(sU[e]) & kAbs;
+    if (li && lj && x <= kInf) {
+      if (i == j) dia = max(dia, x);
+      else off = max(off, x);
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) atomicMax(&counters[3], (unsigned long long)__double_as_longlong(mx));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off = max(off, __shfl_xor_sync(0xffffffffu, off, o));
+    dia = max(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+  }
+  if (lane == 0) {
+    const double mx = fmax(__longlong_as_double(off), 2.0 * __longlong_as_double(dia));
+    atomicMax(&counters[3], (unsigned long long)__double_as_longlong(mx));
   }
 }
 
-// Rows ib0, ib0 + step, ... (< n) of P <- P (I - U), g lanes per row; Pf: float32 copy.  Uniform
-// trip count for the CTA; row values are exchanged with shuffles so that no lane reads an element
-// another lane has already overwritten.
+// Rows ib0, ib0 + step, ... (< n) of P <- P (I - U), g lanes per row; Pf: float32 copy.  The trip
+// count is uniform within a warp (a warp stops once none of its rows is left); row values are
+// exchanged with shuffles so that no lane reads an element another lane has already overwritten.
 __device__ void correct_rows(const double* __restrict__ sU, double* __restrict__ P, int b, int g, int ib0,
                              int ib_end, int step, float* __restrict__ Pf) {
   const int rl = threadIdx.x / g, d = threadIdx.x - rl * g;
   const int gbase = (threadIdx.x & 31) & ~(g - 1);
+  const int wrow = (threadIdx.x & ~31) / g;   // first row of this warp within an iteration
   for (int ib = ib0; ib < ib_end; ib += step) {
+    if (ib + wrow >= ib_end) break;            // no row of this warp is left (warp-uniform)
     const int i = ib + rl;
     const bool live = i < ib_end && d < b;
     const double p = live ? P[(long long)i * b + d] : 0.0;
@@ -417,7 +437,8 @@ k_correct(const double* __restrict__ G3, const double* __restrict__ R1, double* 
   if (blockIdx.x == 0)   // only block 0 forms the product with R1
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) sR[e] = R1[e];
   __syncthreads();
-  if (blockIdx.x == 0) correct_coefs(sU, sR, b, Tdiag, ldT, Rout, nullptr, G3, counters);
+  if (blockIdx.x == 0) correct_coefs(sU, sR, b, Tdiag, ldT, Rout, nullptr);
+  if (blockIdx.x == 0 && counters && threadIdx.x < 32) correct_defect(sU, b, counters);
   const int rows_per_block = ORTH_T / g;
   correct_rows(sU, P, b, g, blockIdx.x * rows_per_block, n, gridDim.x * rows_per_block, Pf);
 }
@@ -562,12 +583,16 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   __syncthreads();
   const int step = ORTH_T / a.g;
   if (!a.twoc) {
-    if (blockIdx.x == 0) correct_coefs(sU, sR, B, a.Tdiag, a.ldT, nullptr, nullptr, a.G3, a.counters);
+    // the coefficients by the last CTA, the defect by the last warp of CTA 0: off the rows'
+    // critical path where a CTA has fewer rows than warps
+    if (blockIdx.x == nb - 1) correct_coefs(sU, sR, B, a.Tdiag, a.ldT, nullptr, nullptr);
+    if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
     correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
     return;
   }
   // two first-order corrections: P^T P = I up to O(|E|^4)
-  correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2, a.G3, blockIdx.x == 0 ? a.counters : nullptr);
+  correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2);
+  if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
   correct_rows(sU, a.P, B, a.g, r0, r1, step, nullptr);
   __syncthreads();
   gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
@@ -576,7 +601,7 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   SVT_BARRIER_OR_RETURN();
   correct_load_U(a.G3, B, sU);
   __syncthreads();
-  if (blockIdx.x == 0) correct_coefs(sU, sR2, B, a.Tdiag, a.ldT, nullptr, nullptr, a.G3, nullptr);
+  if (blockIdx.x == nb - 1) correct_coefs(sU, sR2, B, a.Tdiag, a.ldT, nullptr, nullptr);
   correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
 }
 
