@@ -16,7 +16,9 @@
 //   * float32 path: rotations in float32 (the float64 rate is 1/64 of float32 on GB300); then, for
 //     the leading nvec right vectors w (renormalised in float64), theta = ||T w|| and
 //     x = T w / theta are formed in float64, so the values compared against tau are float64
-//     Rayleigh quotients, exact to second order in the float32 angle error of w.
+//     Rayleigh quotients, exact to second order in the float32 angle error of w.  The rotations act
+//     on the rows of T (the columns of T^T), so the rotated columns are the right vectors; the
+//     rotations themselves (the left vectors) are not accumulated.
 // Residual estimates of the Lanczos relation: res_k = || S x_k[last b rows] || with S the b x b
 // upper triangular factor of the last block (Y^T U_J = V T^T + V_{J+1} S E_J^T).
 #include <mutex>
@@ -88,7 +90,7 @@ __device__ __forceinline__ float shfl_xor_r(float v, int o) { return __shfl_xor_
 __device__ __forceinline__ double shfl_xor_r(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 
 // Sweeps of the one-sided Jacobi method on G (K x K, column-major in shared memory), accumulating
-// the rotations in W.  JL lanes per column pair (JR = ceil(96 / JL) rows each), 32 / JL pairs per
+// the rotations in W when ACC (otherwise W is not touched).  JL lanes per column pair (JR = ceil(96 / JL) rows each), 32 / JL pairs per
 // warp: the rotation parameters of four pairs come out of one warp instruction, and the inner
 // products need only log2(JL) butterfly steps.  Returns the number of sweeps taken.
 static constexpr int JL = 8;
@@ -96,7 +98,7 @@ static constexpr int JL = 8;
 template <typename R>
 __device__ __forceinline__ R shfl_grp(R v, int o) { return shfl_xor_r(v, o); }
 
-template <typename R, int JR>   // JR = rows per lane = ceil(K / JL), a compile-time bound
+template <typename R, int JR, bool ACC>   // JR = rows per lane = ceil(K / JL), a compile-time bound
 __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gl = lane & (JL - 1);                 // lane inside the pair group
@@ -129,8 +131,8 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
           const bool in = has && r < K;
           a[k] = in ? gp[r] : R(0);
           bq[k] = in ? gq[r] : R(0);
-          wa[k] = in ? wp[r] : R(0);
-          wb[k] = in ? wq[r] : R(0);
+          wa[k] = (ACC && in) ? wp[r] : R(0);
+          wb[k] = (ACC && in) ? wq[r] : R(0);
         }
 #pragma unroll
         for (int k = 0; k < JR; ++k) {
@@ -156,8 +158,10 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
               if (r < K) {
                 gp[r] = c * a[k] - s * bq[k];
                 gq[r] = s * a[k] + c * bq[k];
-                wp[r] = c * wa[k] - s * wb[k];
-                wq[r] = s * wa[k] + c * wb[k];
+                if (ACC) {
+                  wp[r] = c * wa[k] - s * wb[k];
+                  wq[r] = s * wa[k] + c * wb[k];
+                }
               }
             }
             if (gl == 0) *flag = 1;
@@ -231,7 +235,7 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
   }
   build_schedule(sched, K);
   __syncthreads();
-  const int sweeps = jacobi_sweeps<double, JR>(G, W, sched, K, tol, max_sweeps, &flag);
+  const int sweeps = jacobi_sweeps<double, JR, true>(G, W, sched, K, tol, max_sweeps, &flag);
   if (threadIdx.x == 0) {
     if (sweeps > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
     if (counters) {
@@ -304,11 +308,14 @@ k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __res
     // trans: the rotations act on the rows of T (the columns of T^T)
     if (trans) G[i * K + c] = (float)v;
     else G[c * K + i] = (float)v;
-    W[c * K + i] = (i == c) ? 1.f : 0.f;
+    if (!trans) W[c * K + i] = (i == c) ? 1.f : 0.f;
   }
   build_schedule(sched, K);
   __syncthreads();
-  const int sweeps = jacobi_sweeps<float, JR>(G, W, sched, K, tol, max_sweeps, &flag);
+  // with trans the accumulated rotations would be the left vectors, which are formed in float64
+  // from T w for the leading nvec triplets instead: W is not accumulated
+  const int sweeps = trans ? jacobi_sweeps<float, JR, false>(G, W, sched, K, tol, max_sweeps, &flag)
+                           : jacobi_sweeps<float, JR, true>(G, W, sched, K, tol, max_sweeps, &flag);
   if (threadIdx.x == 0) {
     if (sweeps > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
     if (counters) {
@@ -382,12 +389,13 @@ k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __res
     }
     if (lane == 0) res[k] = sqrt(r2);
   }
-  // remaining triplets (not used by the rank policy): float32 values and vectors
+  // remaining triplets (not used by the rank policy, the restart or the shrink): float32 values
+  // and right vectors; with trans no left vectors (zero columns of Xl)
   for (int e = threadIdx.x; e < (K - nvec) * K; e += blockDim.x) {
     const int kk = nvec + e / K, i = e % K;
     const int c = order[kk];
     const float th = nrm[c];
-    Xl[i * K + kk] = trans ? (double)Lv[c * K + i] : (th > 0.f ? (double)(Lv[c * K + i] / th) : 0.0);
+    Xl[i * K + kk] = trans ? 0.0 : (th > 0.f ? (double)(Lv[c * K + i] / th) : 0.0);
     Wr[i * K + kk] = trans ? (th > 0.f ? (double)(Rv[c * K + i] / th) : 0.0) : (double)Rv[c * K + i];
   }
   for (int kk = nvec + threadIdx.x; kk < K; kk += blockDim.x) {
