@@ -16,7 +16,9 @@
 //                                       ill conditioned; the host then adds a second step 3, giving
 //                                       O(|E|^4))
 // The coefficients satisfy P_in = Q (C1 + C2) + P_out R2 R1 exactly for the factors used; C1 + C2
-// and R2 R1 are the entries of the projected block bidiagonal matrix.
+// and R2 R1 are the entries of the projected block bidiagonal matrix.  Of each P^T P only what is
+// used is formed: its diagonal in step 1 (the deflation reference), its upper triangle in steps 2
+// and 3 (the Cholesky factor and U(E) read nothing else).
 #include <algorithm>
 #include <mutex>
 
@@ -62,12 +64,37 @@ long long gram_partial_doubles(int n, int nq, int b) {
   return nblk * (long long)(nq + 1) * b * b;
 }
 
-// Partial Gram of rows [r0, r1) into partial[blockIdx.x * E ...).  Called by all threads.
+// Entry layout of a Gram G = [Q_0 .. Q_{nq-1}, P]^T P: the nq b x b blocks Q_k^T P row-major,
+// then of P^T P only what is used: its diagonal (the squared column norms before the projection,
+// `first` pass) or its upper triangle (i <= j) folded into b / 2 rows of b + 1 entries: row r
+// holds (r, r .. b-1) followed by (b-1-r, b-1-r .. b-1), so both directions of the index map are
+// a division by b + 1 and a comparison (b is even).
+__host__ __device__ __forceinline__ int gram_entries(int nq, int b, bool first) {
+  return nq * b * b + (first ? b : b * (b + 1) / 2);
+}
+__host__ __device__ __forceinline__ int upper_index(int i, int j, int b) {
+  return i < b / 2 ? i * (b + 1) + (j - i) : (b - 1 - i) * (b + 1) + (j + 1);
+}
+// (i, j) of entry t of the folded upper triangle of a b x b matrix
+__device__ __forceinline__ void upper_ij(int t, int b, int& i, int& j) {
+  const int r = t / (b + 1), q = t - r * (b + 1);
+  if (q < b - r) {
+    i = r;
+    j = r + q;
+  } else {
+    i = b - 1 - r;
+    j = q - 1;
+  }
+}
+
+// Partial Gram of rows [r0, r1) into partial[blockIdx.x * E ...), E = gram_entries(nq, b, first).
+// Called by all threads.
 __device__ void gram_chunk(const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ P,
-                           int b, int r0, int r1, double* __restrict__ partial) {
+                           int b, int r0, int r1, double* __restrict__ partial, bool first) {
   __shared__ double tile[GRAM_SUB][GRAM_MAXW];
   const int W = (nq + 1) * b;
-  const int E = W * b;
+  const int E = gram_entries(nq, b, first);
+  const int EQ = nq * b * b;
   double acc[GRAM_EPT];
 #pragma unroll
   for (int k = 0; k < GRAM_EPT; ++k) acc[k] = 0.0;
@@ -88,7 +115,17 @@ __device__ void gram_chunk(const double* __restrict__ Q, long long q_stride, int
     for (int k = 0; k < GRAM_EPT; ++k) {
       int e = threadIdx.x + k * ORTH_T;
       if (e < E) {
-        int c = e / b, d = e - c * b;
+        int c, d;
+        if (e < EQ) {
+          c = e / b;
+          d = e - c * b;
+        } else if (first) {
+          c = nq * b + (e - EQ);
+          d = e - EQ;
+        } else {
+          upper_ij(e - EQ, b, c, d);
+          c += nq * b;
+        }
         double s = acc[k];
         for (int rr = 0; rr < nr; ++rr) s += tile[rr][c] * tile[rr][nq * b + d];
         acc[k] = s;
@@ -107,7 +144,7 @@ __global__ void __launch_bounds__(ORTH_T)
 k_gram_partial(const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ P, int n, int b,
                int rows_per_cta, double* __restrict__ partial) {
   const int r0 = blockIdx.x * rows_per_cta;
-  gram_chunk(Q, q_stride, nq, P, b, r0, min(n, r0 + rows_per_cta), partial);
+  gram_chunk(Q, q_stride, nq, P, b, r0, min(n, r0 + rows_per_cta), partial, nq > 0);
 }
 
 // CTA x owns 32 entries; its four warps sum the partials k = w, w + 4, ... and combine in a fixed
@@ -156,7 +193,7 @@ int launch_gram(const double* Q, long long q_stride, int nq, const double* P, in
   const int rows = gram_rows_per_cta(n);
   const int nblk = (n + rows - 1) / rows;
   k_gram_partial<<<nblk, ORTH_T, 0, st>>>(Q, q_stride, nq, P, n, b, rows, partial);
-  return 1 + gram_reduce_launch(partial, nblk, (nq + 1) * b * b, G, st, Gprev, Tcol, ldT, nq * b * b, b);
+  return 1 + gram_reduce_launch(partial, nblk, gram_entries(nq, b, nq > 0), G, st, Gprev, Tcol, ldT, nq * b * b, b);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -167,7 +204,8 @@ int launch_gram(const double* Q, long long q_stride, int nq, const double* P, in
 // ------------------------------------------------------------------------------------------------
 // Rows [r0, r1) of P, g lanes per row (lane d owns column d < b):
 //   mode 0: P <- P - Q C;   mode 1: P <- (P - Q C) R^-1 with dinv = 1 / diag(R)
-// C (nq b x b), R (b x b) and dinv (b) in shared memory.  Called by all threads of the CTA.
+// C (nq b x b), sR = R diag(dinv) (the columns of R scaled by the reciprocal pivots, b x b) and
+// dinv (b) in shared memory.  Called by all threads of the CTA.
 __device__ void update_rows(int mode, const double* __restrict__ Q, long long q_stride, int nq,
                             const double* __restrict__ sC, const double* __restrict__ sR,
                             const double* __restrict__ sD, double* __restrict__ P, int b, int g, int r0, int r1,
@@ -202,15 +240,15 @@ __device__ void update_rows(int mode, const double* __restrict__ Q, long long q_
       v = P[(long long)i * b + d] - ((a0 + a1) + (a2 + a3));
     }
     if (mode == 1) {
-      // forward substitution: out_e = (v_e - sum_{k<e} out_k R[k][e]) * dinv[e]
-      double out = 0.0;
+      // forward substitution out_d = (v_d - sum_{e<d} out_e R[e][d]) dinv[d], written as
+      // w = v dinv, w_d -= out_e (R[e][d] dinv[d]): one float64 operation per step, and lane e
+      // holds out_e once the steps before it are done
+      double w = d < b ? v * sD[d] : 0.0;
       for (int e = 0; e < b; ++e) {
-        const double oe = v * sD[e];
-        const double ob = __shfl_sync(0xffffffffu, oe, gbase + e);
-        if (d == e) out = ob;
-        if (d > e) v -= ob * sR[e * b + d];
+        const double ob = __shfl_sync(0xffffffffu, w, gbase + e);
+        if (d > e && d < b) w -= ob * sR[e * b + d];
       }
-      v = out;
+      v = w;
     }
     if (live) P[(long long)i * b + d] = v;
   }
@@ -226,7 +264,8 @@ k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq
   const int K = nq * b;
   for (int t = threadIdx.x; t < K * b; t += blockDim.x) sC[t] = C[t];
   if (mode == 1) {
-    for (int t = threadIdx.x; t < b * b; t += blockDim.x) sR[t] = R[t];
+    // R diag(dinv): the columns of R scaled by the reciprocal pivots
+    for (int t = threadIdx.x; t < b * b; t += blockDim.x) sR[t] = R[t] * dinv[t % b];
     for (int t = threadIdx.x; t < b; t += blockDim.x) sD[t] = dinv[t];
   }
   __syncthreads();
@@ -234,7 +273,7 @@ k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq
   const int r1 = min(n, r0 + rows_per_cta);
   update_rows(mode, Q, q_stride, nq, sC, sR, sD, P, b, g, r0, r1);
   __syncthreads();
-  gram_chunk(Q, q_stride, mode == 0 ? nq : 0, P, b, r0, r1, partial);
+  gram_chunk(Q, q_stride, mode == 0 ? nq : 0, P, b, r0, r1, partial, false);
 }
 
 int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, const double* C, const double* R,
@@ -245,7 +284,7 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
   const int nblk = (n + rows - 1) / rows;
   k_update_gram<<<nblk, ORTH_T, 0, st>>>(mode, Q, q_stride, nq, C, R, dinv, P, n, b, g, rows, partial);
   const int nqg = mode == 0 ? nq : 0;
-  const int E = (nqg + 1) * b * b;
+  const int E = gram_entries(nqg, b, false);
   return 1 + gram_reduce_launch(partial, nblk, E, G, st, Gprev, Tcol, ldT, nqg * b * b, b);
 }
 
@@ -298,9 +337,11 @@ __device__ __forceinline__ void chol_warp(const double* __restrict__ G1, const d
 #pragma unroll
   for (int s = 0; s < NR; ++s) {
     const int i = s * H + h;
-    a[s] = (col && i < B && i <= c) ? __ldcg(G2 + (K + i) * B + c) : 0.0;
+    a[s] = (col && i < B && i <= c) ? __ldcg(G2 + K * B + upper_index(i, c, B)) : 0.0;
   }
-  const double ref = col ? ((G1 && nq > 0) ? __ldcg(G1 + (K + c) * B + c) : __ldcg(G2 + (K + c) * B + c)) : 0.0;
+  // the column's squared norm before the projections (diagonal layout of the first pass)
+  const double ref = col ? ((G1 && nq > 0) ? __ldcg(G1 + K * B + c) : __ldcg(G2 + K * B + upper_index(c, c, B)))
+                         : 0.0;
   const long long thr = __double_as_longlong(DEFLATE_REL2 * ref);
   int deflated = 0;
 #pragma unroll
@@ -340,12 +381,17 @@ k_chol(const double* __restrict__ G1, const double* __restrict__ G2, int nq, dou
 // P <- P (I - U(E)) with E = G3 - I; (I + U(E)) R1 (upper triangular) goes to Tdiag and/or Rout,
 // and max |E| over non-deflated columns to counters[3].
 // ------------------------------------------------------------------------------------------------
-// sU = U(E) (upper triangle of E, halved diagonal), from G3 read through L2.  All threads.
+// sU = U(E) (upper triangle of E, halved diagonal; b x b row-major), from G3 (upper-triangle
+// layout) read through L2.  All threads.
 __device__ __forceinline__ void correct_load_U(const double* __restrict__ G3, int b, double* __restrict__ sU) {
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     int i = e / b, j = e - i * b;
-    double x = __ldcg(G3 + e) - (i == j ? 1.0 : 0.0);
-    sU[e] = (j > i) ? x : ((i == j) ? 0.5 * x : 0.0);
+    double v = 0.0;
+    if (j >= i) {
+      const double x = __ldcg(G3 + upper_index(i, j, b)) - (i == j ? 1.0 : 0.0);
+      v = (j > i) ? x : 0.5 * x;
+    }
+    sU[e] = v;
   }
 }
 
@@ -533,7 +579,7 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   double* sC = sm_orth;                 // K x B coefficients (C1, then C2)
   double* sR = sC + OB_MAXK * B;        // R1
   double* sU = sR + B * B;              // U(E)
-  double* sR2 = sU + B * B;             // (I + U(E)) R1 of a first correction
+  double* sR2 = sU + B * B;             // R1 diag(1 / diag(R1)); then (I + U(E)) R1 of a first correction
   double* sD = sR2 + B * B;             // 1 / diag(R1)
   // a barrier of an earlier cooperative kernel gave up: the whole grid returns at once
   if (*(volatile unsigned int*)a.err & SVT_DEVERR_BARRIER) return;
@@ -542,25 +588,24 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   const int r0 = blockIdx.x * a.rpc;
   const int r1 = min(a.n, r0 + a.rpc);
   if (a.nq > 0) {
-    const int E1 = (a.nq + 1) * B * B;
-    // C1 = Q^T P (with P^T P)
-    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial);
+    // C1 = Q^T P (with the diagonal of P^T P)
+    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, true);
     SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, E1, a.G1, nullptr, nullptr, 0, 0, B);
+    reduce_entries(a.partial, nb, gram_entries(a.nq, B, true), a.G1, nullptr, nullptr, 0, 0, B);
     SVT_BARRIER_OR_RETURN();
     // P <- P - Q C1; [C2; A] = [Q, P]^T P; coefficients C1 + C2 -> Tcol
     for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G1 + t);
     __syncthreads();
     update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1);
     __syncthreads();
-    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial);
+    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, false);
     SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, E1, a.G2, a.G1, a.Tcol, a.ldT, K * B, B);
+    reduce_entries(a.partial, nb, gram_entries(a.nq, B, false), a.G2, a.G1, a.Tcol, a.ldT, K * B, B);
     SVT_BARRIER_OR_RETURN();
   } else {
-    gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+    gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
     SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, B * B, a.G2, nullptr, nullptr, 0, 0, B);
+    reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G2, nullptr, nullptr, 0, 0, B);
     SVT_BARRIER_OR_RETURN();
   }
   // R1 = chol(A) in every CTA, by warp 0, while warps 1.. project P <- P - Q C2; then
@@ -573,11 +618,13 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
     update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1, 32, ORTH_T - 32);
   }
   __syncthreads();
-  update_rows(1, nullptr, 0, 0, nullptr, sR, sD, a.P, B, a.g, r0, r1);
+  for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR2[t] = sR[t] * sD[t % B];
   __syncthreads();
-  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+  update_rows(1, nullptr, 0, 0, nullptr, sR2, sD, a.P, B, a.g, r0, r1);
+  __syncthreads();
+  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
   SVT_BARRIER_OR_RETURN();
-  reduce_entries(a.partial, nb, B * B, a.G3, nullptr, nullptr, 0, 0, B);
+  reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
   SVT_BARRIER_OR_RETURN();
   correct_load_U(a.G3, B, sU);
   __syncthreads();
@@ -595,9 +642,9 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
   correct_rows(sU, a.P, B, a.g, r0, r1, step, nullptr);
   __syncthreads();
-  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial);
+  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
   SVT_BARRIER_OR_RETURN();
-  reduce_entries(a.partial, nb, B * B, a.G3, nullptr, nullptr, 0, 0, B);
+  reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
   SVT_BARRIER_OR_RETURN();
   correct_load_U(a.G3, B, sU);
   __syncthreads();
