@@ -120,6 +120,7 @@ struct svt_ctx {
   // Lanczos workspace
   double *Ub = nullptr, *Vb = nullptr;   // block bases (blocks of rows x b)
   double *T = nullptr, *S = nullptr, *theta = nullptr, *Xl = nullptr, *Wr = nullptr, *res = nullptr;
+  float* wsrc = nullptr;   // float32 leading Ritz vectors of the projected SVD (kBMax x kKMax)
   double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
   double *Rkeep = nullptr, *scale = nullptr;
   bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
@@ -477,8 +478,8 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
     if (c->prec == SVT_FP64)
       return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
                               c->dcount, c->st);
-    return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, b, 2e-6, 60, c->err,
-                                  c->dcount, c->st);
+    return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, b, c->wsrc, 2e-6, 60,
+                                  c->err, c->dcount, c->st);
   });
   TRY(launched(c, l));
   CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
@@ -910,6 +911,7 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
   TRY(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
   TRY(dalloc_t(c, &c->res, kKMax));
+  TRY(dalloc_t(c, &c->wsrc, (size_t)kBMax * kKMax));
   TRY(dalloc_t(c, &c->G1, 128 * 32));
   TRY(dalloc_t(c, &c->G2, 128 * 32));
   TRY(dalloc_t(c, &c->G3, 128 * 32));
@@ -969,6 +971,7 @@ extern "C" size_t svt_estimate_device_bytes(int64_t m, int64_t n, int64_t nnz, c
   if (o.precision != SVT_FP64) b += 4 * (M + N) * kBMax + 4 * (M + N) * ((cap + 3) & ~3);
   b += 8 * (M + N) * (kKMax + kBMax);                        // Lanczos bases
   b += 8 * (3 * kKMax * kKMax + kKMax * kBMax + 3 * 128 * 32 + 3 * kBMax * kBMax + 256 + 4096);
+  b += 4 * kBMax * kKMax;                                    // float32 Ritz vectors of the projected SVD
   b += 8 * (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax);
   // scratch of the structure build, peak (host inputs staged as int32, int32, float64)
   const size_t nmax = std::max(M, N) + 1;

@@ -108,10 +108,12 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, do
 // capture); returns 0 on success.
 int init_jacobi_attributes();
 
-// Float32-rotation Jacobi with float64 Ritz values for the leading nvec triplets (see dense.cu).
+// Float32-rotation Jacobi with float64 Ritz values for the leading nvec triplets (jacobi.cu); two
+// launches: the sweeps (one CTA), then the float64 refinement (nvec CTAs).  wsrc: nvec x K floats
+// of scratch.
 int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,
-                           double* Wr, double* res, int nvec, double tol, int max_sweeps, unsigned int* err,
-                           unsigned long long* counters, cudaStream_t st);
+                           double* Wr, double* res, int nvec, float* wsrc, double tol, int max_sweeps,
+                           unsigned int* err, unsigned long long* counters, cudaStream_t st);
 
 // Out (n x s) = sum over blocks i of B_i (n x b) W[i b .. i b + b, 0 .. s) , columns scaled by
 // scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).  OutF (may be NULL):

@@ -288,14 +288,11 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
 // ------------------------------------------------------------------------------------------------
 template <int JR>
 __global__ void __launch_bounds__(512)
-k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
-               double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
-               int nvec, float tol, int max_sweeps, unsigned int* err, unsigned long long* counters, int trans) {
+k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, double* __restrict__ theta, double* __restrict__ Xl,
+               double* __restrict__ Wr, double* __restrict__ res, int nvec, float* __restrict__ wsrc, float tol,
+               int max_sweeps, unsigned int* err, unsigned long long* counters, int trans) {
   extern __shared__ double smm[];
-  double* Td = smm;                         // K x K row-major, float64
-  double* wv = Td + K * K;                  // nvec x K normalised right vectors (float64)
-  double* gx = wv + nvec * K;               // nvec x K: T w
-  float* G = (float*)(gx + nvec * K);       // K x K column-major
+  float* G = (float*)smm;                   // K x K column-major
   float* W = G + K * K;                     // K x K column-major
   float* nrm = W + K * K;                   // K
   int* order = (int*)(nrm + K);             // K
@@ -304,7 +301,6 @@ k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __res
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int i = e / K, c = e - i * K;
     const double v = T[i * ldT + c];
-    Td[e] = v;
     // trans: the rotations act on the rows of T (the columns of T^T)
     if (trans) G[i * K + c] = (float)v;
     else G[c * K + i] = (float)v;
@@ -334,60 +330,12 @@ k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __res
   sort_columns<float>(nrm, order, K);
   __syncthreads();
   // right singular vectors of T: the accumulated rotations W, or with trans the rotated columns
-  // of T^T; the leading nvec are normalised in float64
+  // of T^T; the leading nvec go to wsrc (float32, in decreasing order) for the float64 refinement
   const float* Rv = trans ? G : W;
   const float* Lv = trans ? W : G;
-  for (int k = warp; k < nvec; k += nw) {
-    const int c = order[k];
-    double s2 = 0.0;
-    for (int i = lane; i < K; i += 32) {
-      const double v = (double)Rv[c * K + i];
-      s2 += v * v;
-    }
-    s2 = warp_sum(s2);
-    const double inv = rsqrt_nr(s2, 2);
-    for (int i = lane; i < K; i += 32) wv[k * K + i] = (double)Rv[c * K + i] * inv;
-  }
-  __syncthreads();
-  // T w: one thread per output entry, four independent accumulation chains
   for (int e = threadIdx.x; e < nvec * K; e += blockDim.x) {
     const int k = e / K, i = e - k * K;
-    const double* trow = Td + i * K;
-    const double* w = wv + k * K;
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    int cc = 0;
-    for (; cc + 3 < K; cc += 4) {
-      v0 += trow[cc] * w[cc];
-      v1 += trow[cc + 1] * w[cc + 1];
-      v2 += trow[cc + 2] * w[cc + 2];
-      v3 += trow[cc + 3] * w[cc + 3];
-    }
-    for (; cc < K; ++cc) v0 += trow[cc] * w[cc];
-    gx[k * K + i] = (v0 + v1) + (v2 + v3);
-  }
-  __syncthreads();
-  for (int k = warp; k < nvec; k += nw) {
-    double s2 = 0.0;
-    for (int i = lane; i < K; i += 32) s2 += gx[k * K + i] * gx[k * K + i];
-    s2 = warp_sum(s2);
-    const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
-    const double inv = th > 0.0 ? rcp_nr(th) : 0.0;
-    for (int i = lane; i < K; i += 32) {
-      Xl[i * K + k] = gx[k * K + i] * inv;
-      Wr[i * K + k] = wv[k * K + i];
-    }
-    if (lane == 0) theta[k] = th;
-    double r2 = 0.0;
-    if (S) {
-      for (int e2 = lane; e2 < b; e2 += 32) {
-        double v = 0.0;
-        for (int d = e2; d < b; ++d) v += S[e2 * b + d] * gx[k * K + (K - b + d)];
-        v *= inv;
-        r2 += v * v;
-      }
-      r2 = warp_sum(r2);
-    }
-    if (lane == 0) res[k] = sqrt(r2);
+    wsrc[e] = Rv[order[k] * K + i];
   }
   // remaining triplets (not used by the rank policy, the restart or the shrink): float32 values
   // and right vectors; with trans no left vectors (zero columns of Xl)
@@ -402,6 +350,69 @@ k_jacobi_mixed(const double* __restrict__ T, int ldT, int K, const double* __res
     theta[kk] = (double)nrm[order[kk]];
     res[kk] = INFINITY;
   }
+}
+
+// Float64 Ritz triplets of the leading nvec right vectors of the float32 Jacobi: one CTA per
+// triplet k (spread over SMs: GB300 runs float64 at 2 FMA per clock per SM).  w = wsrc_k
+// normalised, x = T w / theta with theta = ||T w|| (a Rayleigh value, exact to second order in the
+// float32 angle error of w), and the Lanczos residual estimate res_k = || S x[last b rows] ||.
+__global__ void __launch_bounds__(128)
+k_ritz_refine(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
+              const float* __restrict__ wsrc, double* __restrict__ theta, double* __restrict__ Xl,
+              double* __restrict__ Wr, double* __restrict__ res) {
+  __shared__ double wv[JMAXK];
+  __shared__ double gx[JMAXK];
+  const int k = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float* w = wsrc + (long long)k * K;
+  if (warp == 0) {
+    double s2 = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      const double v = (double)w[i];
+      s2 += v * v;
+    }
+    s2 = warp_sum(s2);
+    const double inv = rsqrt_nr(s2, 2);
+    for (int i = lane; i < K; i += 32) wv[i] = (double)w[i] * inv;
+  }
+  __syncthreads();
+  // T w: one thread per row, four independent accumulation chains
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double* trow = T + (long long)i * ldT;
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int cc = 0;
+    for (; cc + 3 < K; cc += 4) {
+      v0 += trow[cc] * wv[cc];
+      v1 += trow[cc + 1] * wv[cc + 1];
+      v2 += trow[cc + 2] * wv[cc + 2];
+      v3 += trow[cc + 3] * wv[cc + 3];
+    }
+    for (; cc < K; ++cc) v0 += trow[cc] * wv[cc];
+    gx[i] = (v0 + v1) + (v2 + v3);
+  }
+  __syncthreads();
+  if (warp != 0) return;
+  double s2 = 0.0;
+  for (int i = lane; i < K; i += 32) s2 += gx[i] * gx[i];
+  s2 = warp_sum(s2);
+  const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
+  const double inv = th > 0.0 ? rcp_nr(th) : 0.0;
+  for (int i = lane; i < K; i += 32) {
+    Xl[i * K + k] = gx[i] * inv;
+    Wr[i * K + k] = wv[i];
+  }
+  if (lane == 0) theta[k] = th;
+  double r2 = 0.0;
+  if (S) {
+    for (int e2 = lane; e2 < b; e2 += 32) {
+      double v = 0.0;
+      for (int d = e2; d < b; ++d) v += S[e2 * b + d] * gx[K - b + d];
+      v *= inv;
+      r2 += v * v;
+    }
+    r2 = warp_sum(r2);
+  }
+  if (lane == 0) res[k] = sqrt(r2);
 }
 
 static int jacobi_threads(int K) {
@@ -430,8 +441,7 @@ bool jacobi_attrs() {
   std::call_once(once, [] {
     const size_t mx64 =
         (size_t)(2 * JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
-    const size_t mxm = (size_t)(JMAXK * JMAXK + 2 * JMAXB * JMAXK) * sizeof(double) +
-                       (size_t)(2 * JMAXK * JMAXK + JMAXK) * sizeof(float) + (size_t)JMAXK * sizeof(int) +
+    const size_t mxm = (size_t)(2 * JMAXK * JMAXK + JMAXK) * sizeof(float) + (size_t)JMAXK * sizeof(int) +
                        sched_bytes(JMAXK);
     set_smem_attrs<3>(mx64, mxm);
     set_smem_attrs<6>(mx64, mxm);
@@ -461,30 +471,30 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, do
 }
 
 int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,
-                           double* Wr, double* res, int nvec, double tol, int max_sweeps, unsigned int* err,
-                           unsigned long long* counters, cudaStream_t st) {
+                           double* Wr, double* res, int nvec, float* wsrc, double tol, int max_sweeps,
+                           unsigned int* err, unsigned long long* counters, cudaStream_t st) {
   if (nvec > K) nvec = K;
   if (nvec > JMAXB) nvec = JMAXB;
   if (!jacobi_attrs()) return 0;  // no launch; the caller's cudaGetLastError check reports the failure
-  const size_t smem = (size_t)(K * K + 2 * nvec * K) * sizeof(double) + (size_t)(2 * K * K + K) * sizeof(float) +
-                      (size_t)K * sizeof(int) + sched_bytes(K);
+  const size_t smem = (size_t)(2 * K * K + K) * sizeof(float) + (size_t)K * sizeof(int) + sched_bytes(K);
   const int thr = jacobi_threads(K);
   const int rpl = (K + JL - 1) / JL;
   const float ft = (float)tol;
   const int tr = kJacobiOnRows;
   if (rpl <= 3)
-    k_jacobi_mixed<3><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters,
+    k_jacobi_mixed<3><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err, counters,
                                             tr);
   else if (rpl <= 6)
-    k_jacobi_mixed<6><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters,
+    k_jacobi_mixed<6><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err, counters,
                                             tr);
   else if (rpl <= 9)
-    k_jacobi_mixed<9><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err, counters,
+    k_jacobi_mixed<9><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err, counters,
                                             tr);
   else
-    k_jacobi_mixed<12><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, nvec, ft, max_sweeps, err,
+    k_jacobi_mixed<12><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err,
                                              counters, tr);
-  return 1;
+  k_ritz_refine<<<nvec, 128, 0, st>>>(T, ldT, K, S, b, wsrc, theta, Xl, Wr, res);
+  return 2;
 }
 
 }  // namespace svt
