@@ -87,6 +87,11 @@ typedef struct svt_options {
                              lanczos_steps */
   double bf16_switch;     /* SVT_BF16 only: relative residual below which the sparse products move
                              from the bfloat16 copies to the float32 values (default 1e-2) */
+  int orth_grid;          /* upper bound on the CTAs of the cooperative orthonormalisation; 0
+                             (default) = two per SM.  Contexts that run side by side on one GPU
+                             (the serving runtime) cap it so that their cooperative kernels are
+                             resident together.  The row chunks of the Gram sums follow the grid,
+                             so results are reproducible for a given value (not across values). */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */

@@ -14,7 +14,9 @@
  * starve).  A job larger than the whole budget is refused at submission (SVT_ERR_OOM).
  *
  * Results: the same contexts, kernels and launch shapes run a job alone or in a mix, and every
- * reduction has a fixed order, so a job's result does not depend on what runs beside it.
+ * reduction has a fixed order, so a job's result does not depend on what runs beside it.  A job
+ * whose options leave orth_grid at 0 gets max(16, 2 SMs / slots): its result is that of an svt
+ * context with that orth_grid (the same for every job of a server, whatever else is running).
  *
  * Threading: the server's calls are thread-safe.  Dry-run servers (options.dry_run) touch no
  * device: a job sleeps for its dry_run_us and occupies dry_run_bytes, for exercising admission and

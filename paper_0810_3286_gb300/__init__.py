@@ -72,7 +72,7 @@ class Solver:
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
                  max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
-                 restart_steps: int = 0, bf16_switch: float = 1e-2):
+                 restart_steps: int = 0, bf16_switch: float = 1e-2, orth_grid: int = 0):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -88,6 +88,7 @@ class Solver:
         opt.block = int(block)
         opt.restart_steps = int(restart_steps)
         opt.bf16_switch = float(bf16_switch)
+        opt.orth_grid = int(orth_grid)
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda

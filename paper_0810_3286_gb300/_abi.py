@@ -51,6 +51,7 @@ class svt_options(ctypes.Structure):
         ("fused_orth", ctypes.c_int),
         ("restart_steps", ctypes.c_int),
         ("bf16_switch", ctypes.c_double),
+        ("orth_grid", ctypes.c_int),
     ]
 
 

@@ -740,6 +740,7 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->fused_orth = 1;
   opt->restart_steps = 0;
   opt->bf16_switch = 1e-2;
+  opt->orth_grid = 0;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -995,6 +996,7 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   if (o.precision != SVT_FP64 && o.precision != SVT_FP32 && o.precision != SVT_BF16)
     return fail(nullptr, SVT_ERR_ARG, "unknown precision");
   if (o.precision == SVT_BF16 && !(o.bf16_switch >= 0.0)) return fail(nullptr, SVT_ERR_ARG, "bf16_switch must be >= 0");
+  if (o.orth_grid < 0) return fail(nullptr, SVT_ERR_ARG, "orth_grid must be >= 0");
   if (o.ell < 1) o.ell = 5;
   if (o.k_max < 1) o.k_max = 1000;
   if (o.lanczos_steps < 1) o.lanczos_steps = 3;
@@ -1019,6 +1021,7 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   } else {
     // the partial-Gram buffer holds at most 2 * 152 row chunks (gram_partial_doubles)
     c->coop_grid = o.fused_orth ? std::min(orth_coop_init(), 2 * 152) : 0;
+    if (c->coop_grid > 0 && o.orth_grid > 0) c->coop_grid = std::min(c->coop_grid, o.orth_grid);
     s = create_body(c, rows, cols, M_omega);
   }
   if (s != SVT_OK) {

@@ -39,6 +39,7 @@ struct Job {
 struct svt_server {
   svt_server_options opt{};
   int device = 0;
+  int orth_grid = 0;   // cooperative-grid cap of a job that leaves svt_options.orth_grid at 0
   size_t budget = 0;
   Clock::time_point t0;
   std::mutex mu;
@@ -71,6 +72,7 @@ struct svt_server {
     svt_options o = j->spec.opt;
     o.stream = st;
     o.indices_on_device = 0;
+    if (o.orth_grid == 0) o.orth_grid = orth_grid;
     svt_ctx* ctx = nullptr;
     svt_status s = svt_create(j->spec.m, j->spec.n, j->spec.nnz, j->rows.data(), j->cols.data(), j->vals.data(), &o,
                               &ctx);
@@ -160,6 +162,15 @@ extern "C" svt_status svt_server_create(const svt_server_options* opt, svt_serve
       return SVT_ERR_CUDA;
     }
     s->budget = o.device_budget ? o.device_budget : (size_t)(0.9 * (double)free_b);
+    // the slots' cooperative orthonormalisations share the GPU: each gets an equal part of two
+    // CTAs per SM (at least 16), so that all of them can be resident at once
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+      (void)cudaGetLastError();
+      delete s;
+      return SVT_ERR_CUDA;
+    }
+    s->orth_grid = std::max(16, 2 * sms / o.slots);
   }
   try {
     for (int i = 0; i < o.slots; ++i) s->workers.emplace_back([s] { s->worker(); });

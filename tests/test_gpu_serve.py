@@ -2,7 +2,8 @@
 
 * Every job's result in a mix of concurrent jobs is the one it gives alone (same status,
   iterations, rank, residual and factors, bit for bit: the same kernels, launch shapes and
-  fixed-order reductions run in both cases), in float32 and float64.
+  fixed-order reductions run in both cases), in float32 and float64.  "Alone" is a context with
+  the cooperative-grid cap the server gives its jobs (max(16, 2 SMs / slots)).
 * With a budget of 2.5 times the largest job's footprint, the footprints in flight never exceed
   it, several jobs are in flight at once, and the jobs finish.
 """
@@ -20,10 +21,15 @@ def _small_jobs(k, seed0):
     return [serving_job(seed0 + i, n_range=(500, 1200), rank_range=(8, 12), c_range=(5.5, 6.0)) for i in range(k)]
 
 
-def _alone(p, precision):
+def _server_orth_grid(slots):
+    import torch
+    return max(16, 2 * torch.cuda.get_device_properties(0).multi_processor_count // slots)
+
+
+def _alone(p, precision, orth_grid=0):
     from paper_0810_3286_gb300 import Solver
     from paper_0810_3286_gb300._abi import SVTError
-    with Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision) as s:
+    with Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision, orth_grid=orth_grid) as s:
         try:
             res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27, raise_on_nonconvergence=False)
             return (0 if res["converged"] else 6), res, s.factors()
@@ -37,7 +43,7 @@ def test_results_same_alone_and_in_mix(cuda, precision, k):
     jobs = _small_jobs(k, 500)
     if precision == "fp64":
         jobs = [serving_job(900 + i, n_range=(150, 300), rank_range=(3, 6), c_range=(5.5, 6.0)) for i in range(k)]
-    alone = [_alone(p, precision) for p in jobs]
+    alone = [_alone(p, precision, _server_orth_grid(4)) for p in jobs]
     with Server(slots=4, keep_factors=True) as srv:
         ids = [srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 27,
                           precision=precision) for p in jobs]
@@ -75,3 +81,20 @@ def test_memory_budget_and_overlap(cuda):
     assert st["peak_bytes"] <= budget
     assert st["peak_running"] >= 2
     assert all(r["residual"] <= 1e-4 for r in res if r["status"] == 0)
+
+
+def test_orth_grid_cap_same_solution(cuda):
+    # a capped cooperative grid changes only the row chunks of the Gram sums (rounding order)
+    from paper_0810_3286_gb300 import Solver
+    from svt_inputs import config_problem
+    p = config_problem("single_1000", 0)
+    out = []
+    for g in (0, 16):
+        with Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision="fp32", orth_grid=g) as s:
+            res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27)
+            U, d, V = s.factors()
+            out.append((res, (U * d) @ V.T))
+    (r0, X0), (r1, X1) = out
+    assert r0["converged"] and r1["converged"] and r0["rank"] == r1["rank"] == 10
+    assert abs(r0["iterations"] - r1["iterations"]) <= 1
+    assert np.linalg.norm(X1 - X0) <= 1e-3 * np.linalg.norm(X0)
