@@ -72,7 +72,8 @@ typedef struct svt_options {
   int k_max;              /* maximum SVT iterations after the kick (default 1000) */
   int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J*b <= 96) */
   int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
-  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-10 FP64, 1e-6 FP32) */
+  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-10 FP64, 1e-5 FP32 and
+                             BF16: ten times the rounding of the float32 sparse products) */
   int indices_on_device;  /* rows/cols/M_omega given to svt_create are device pointers */
   int use_graphs;         /* replay each Lanczos cycle as a captured CUDA graph (default 1) */
   uint64_t seed;          /* seed of the random start columns of the Lanczos blocks */
