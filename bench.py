@@ -88,7 +88,8 @@ class ClockSampler:
     def __init__(self, device_index):
         self.device_index = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        log_dir = os.environ.get("SVT_BENCH_LOG_DIR", os.path.join(ROOT, "bench_logs"))
+        self.path = os.path.join(log_dir, "clocks_rank%d.csv" % device_index)
 
     def start(self):
         try:
