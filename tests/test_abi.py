@@ -67,3 +67,37 @@ def test_create_rejects_bad_arguments_before_any_device_work(libpath):
     st = L.svt_create(4, 5, 21, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, None, ctypes.byref(ctx))
     assert st == _abi.SVT_ERR_ARG
     assert b"nnz" in L.svt_last_error(None)
+
+
+def test_binding_struct_layouts_match_the_headers(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets that a C compiler gives
+    the header's struct (a field added on one side only would shift the ones after it)."""
+    import ctypes
+    import shutil
+    from paper_0810_3286_gb300 import _abi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [_abi.svt_options, _abi.svt_step_info, _abi.svt_result, _abi.svt_server_options, _abi.svt_job,
+               _abi.svt_job_result, _abi.svt_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "svt.h"', '#include "svt_serve.h"',
+             'int main(void) {']
+    for s in structs:
+        name = s.__name__
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in s._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append('  return 0;\n}')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for s in structs:
+        name = s.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(s), name
+        for f, _ in s._fields_:
+            assert got[(name, f)] == getattr(s, f).offset, (name, f)
