@@ -358,10 +358,14 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
     // one cooperative kernel: gram / update / Cholesky / update / correction phases with grid
     // barriers (same arithmetic as the launch sequence below)
     const double bytes = 8.0 * rows * b * (3.0 * (nq + 1) + 2.0 * nq + 3.0);
-    // float64 flops of the phases: Grams 2 (nq+1) b^2 + 2 (nq+1) b^2 + 2 b^2, updates 2 nq b^2 +
-    // (2 nq + 1) b^2, correction b^2 per row (nq = 0: 6 b^2); a second correction adds 3 b^2
-    const double per_row = (nq > 0 ? 8.0 * nq + 8.0 : 6.0) + (c->two_corrections ? 3.0 : 0.0);
-    const double flops = per_row * (double)rows * b * b;
+    // float64 flops the algorithm needs per row: Grams 2 nq b^2 + 2 b (first pass, diagonal of
+    // P^T P), 2 nq b^2 + b (b + 1) (second pass, upper triangle), b (b + 1) (after the Cholesky);
+    // projections 2 nq b^2 twice; forward substitution b^2; correction b^2.  A second correction
+    // adds b (b + 1) + b^2.
+    const double bb = (double)b * b, bu = (double)b * (b + 1);
+    const double per_row = 8.0 * nq * bb + (nq > 0 ? 2.0 * b : 0.0) + 2.0 * bu + 2.0 * bb +
+                           (c->two_corrections ? bu + bb : 0.0);
+    const double flops = per_row * (double)rows;
     l += prof_launch_f(c, SVT_PROF_ORTH, bytes, flops, [&] {
       return launch_orth_coop(P, Q, q_stride, nq, rows, b, c->gpart, c->G1, c->G2, c->G3, Tcol, Tdiag, kKMax, Pf,
                               c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st);
