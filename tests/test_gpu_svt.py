@@ -48,9 +48,9 @@ def test_shrink_matches_definition(cuda, precision, tol):
     s.close()
 
 
-def _run_parity(p, precision, k0, trace, tau, delta):
+def _run_parity(p, precision, k0, trace, tau, delta, **solver_kw):
     from paper_0810_3286_gb300 import Solver
-    s = Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision)
+    s = Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision, **solver_kw)
     s.configure(tau, delta, 1e-4, 27, k0)
     errs, ranks, stopped_at = [], [], None
     for rec in trace:
@@ -94,6 +94,20 @@ def test_parity_fp64_ragged_rectangular(cuda):
     ref = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, tau, delta, k_max=40, eps=1e-4)
     s, errs, ranks, _ = _run_parity(p, "fp64", ref.k0, ref.trace, tau, delta)
     assert max(errs) <= 1e-5
+    assert all(a == b for a, b in ranks)
+    s.close()
+
+
+@pytest.mark.parametrize("variant", [{"fused_orth": False}, {"use_graphs": False}, {"orth_grid": 8}])
+def test_parity_fp64_other_launch_paths(cuda, variant):
+    """The eight-kernel orthonormalisation (fused_orth = 0, the path taken without cooperative
+    launches), kernel-by-kernel launches without CUDA graphs, and a small cooperative grid give
+    the same iterates as the oracle."""
+    p = planted_problem(173, 131, 3, 3 * 5 * (173 + 131 - 3), seed=12)
+    tau, delta = p.tau_default(), p.delta_default()
+    ref = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, tau, delta, k_max=25, eps=1e-4)
+    s, errs, ranks, _ = _run_parity(p, "fp64", ref.k0, ref.trace, tau, delta, **variant)
+    assert max(errs) <= 1e-5, (variant, max(errs))
     assert all(a == b for a, b in ranks)
     s.close()
 
