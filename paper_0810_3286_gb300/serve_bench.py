@@ -1,13 +1,13 @@
 """Serving measurement: a stream of completion jobs through the serving runtime.
 
-    python -m paper_0810_3286_gb300.serve_bench [--jobs 100] [--slots 8] [--load 0.8] [--single 8]
+    python -m paper_0810_3286_gb300.serve_bench [--jobs 100] [--slots 8] [--loads 0.5,0.8,0.95] [--single 8]
 
 Jobs follow the serving workload: m, n uniform in [500, 8000], rank uniform in 5..20,
 |Omega| = c r (m + n - r) with c uniform in [4, 6], N(0,1) planted factors, eps = 1e-4,
 tau = 5 sqrt(m n), delta = 1.2 m n / |Omega|.  Three measurements on the same jobs:
   * saturated: all jobs submitted at once; mu = completed jobs per second;
-  * Poisson: arrivals at load x mu (exponential gaps), time to eps of every job measured from its
-    arrival, p50 / p99 by nearest rank;
+  * Poisson: arrivals at load x mu (exponential gaps) for every load of --loads, time to eps of
+    every job measured from its arrival, p50 / p99 by nearest rank;
   * one job at a time (slots = 1) in float32 and in float64 on the first `--single` jobs: mean time
     to eps per job, the plain single-job baseline.
 Every job is capped at K_MAX = 500 SVT iterations; jobs that end without meeting the stopping rule
@@ -48,19 +48,10 @@ def _closed_loop(jobs, slots, precision):
     return st, res
 
 
-def run(n_jobs=100, slots=8, load=0.8, n_single=8, seed=0):
+def _poisson(jobs, slots, rate, seed):
     from paper_0810_3286_gb300.serve import Server
-    from svt_inputs import serving_job
-    jobs = [serving_job(seed * 1_000_003 + i) for i in range(n_jobs)]
-    nnz_mean = float(np.mean([p.nnz for p in jobs]))
-    # warm-up: library load, first contexts
-    _closed_loop(jobs[:2], 2, "fp32")
-    sat, res = _closed_loop(jobs, slots, "fp32")
-    mu = sat["solves_per_s"]
-    failed = sum(1 for r in res if r["status"] != 0)
-    # Poisson arrivals at load * mu
-    rng = np.random.default_rng(np.random.PCG64(seed + 17))
-    gaps = rng.exponential(1.0 / (load * mu), size=n_jobs)
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, size=len(jobs))
     with Server(slots=slots) as srv:
         ids = []
         t_next = time.perf_counter()
@@ -71,9 +62,27 @@ def run(n_jobs=100, slots=8, load=0.8, n_single=8, seed=0):
                 time.sleep(dt)
             ids.append(_submit(srv, p, "fp32"))
         srv.drain()
-        poi = srv.stats()
+        st = srv.stats()
         for i in ids:
             srv.wait(i)
+    return st
+
+
+def run(n_jobs=100, slots=8, loads=(0.5, 0.8, 0.95), n_single=8, seed=0):
+    from svt_inputs import serving_job
+    jobs = [serving_job(seed * 1_000_003 + i) for i in range(n_jobs)]
+    nnz_mean = float(np.mean([p.nnz for p in jobs]))
+    # warm-up: library load, first contexts
+    _closed_loop(jobs[:2], 2, "fp32")
+    sat, res = _closed_loop(jobs, slots, "fp32")
+    mu = sat["solves_per_s"]
+    failed = sum(1 for r in res if r["status"] != 0)
+    poisson = []
+    for load in loads:
+        poi = _poisson(jobs, slots, load * mu, seed + 17)
+        poisson.append({"load": load, "arrival_rate_per_s": load * mu, "solves_per_s": poi["solves_per_s"],
+                        "p50_ms": poi["p50_ms"], "p99_ms": poi["p99_ms"], "mean_ms": poi["mean_ms"],
+                        "completed": poi["completed"], "failed": poi["failed"]})
     single = {}
     for prec in ("fp32", "fp64"):
         st, r = _closed_loop(jobs[:n_single], 1, prec)
@@ -88,9 +97,7 @@ def run(n_jobs=100, slots=8, load=0.8, n_single=8, seed=0):
         "saturated": {"solves_per_s": mu, "p50_ms": sat["p50_ms"], "p99_ms": sat["p99_ms"],
                       "peak_jobs_in_flight": sat["peak_running"], "peak_device_bytes": sat["peak_bytes"],
                       "failed": failed},
-        "poisson": {"load": load, "arrival_rate_per_s": load * mu, "solves_per_s": poi["solves_per_s"],
-                    "p50_ms": poi["p50_ms"], "p99_ms": poi["p99_ms"], "mean_ms": poi["mean_ms"],
-                    "completed": poi["completed"], "failed": poi["failed"]},
+        "poisson": poisson,
         "one_job_at_a_time": single,
     }
 
@@ -99,13 +106,14 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--jobs", type=int, default=100)
     ap.add_argument("--slots", type=int, default=8)
-    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--loads", default="0.5,0.8,0.95", help="Poisson loads as fractions of the saturated rate")
     ap.add_argument("--single", type=int, default=8)
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     from paper_0810_3286_gb300 import build
     build.build()
-    print(json.dumps(run(args.jobs, args.slots, args.load, args.single, args.seed)))
+    loads = tuple(float(x) for x in args.loads.split(",") if x)
+    print(json.dumps(run(args.jobs, args.slots, loads, args.single, args.seed)))
 
 
 if __name__ == "__main__":
