@@ -6,9 +6,10 @@
 // root ~650), so the sequence avoids long float64 dependency chains on a single SM:
 //   1. C1 = Q^T P                      (Gram, all SMs)
 //   2. P <- P - Q C1, [C2; A] = [Q, P]^T P   (one fused kernel: update + Gram of the same rows)
-//      R1 = chol(A)                    (one warp; float32 reciprocal square-root seed + one float64
-//                                       Newton step per pivot; columns that lost all but 1e-12 of
-//                                       their norm to the projections are deflated to zero)
+//      R1 = chol(A)                    (one warp; reciprocal square root of each pivot seeded from
+//                                       its bits through a float32 rsqrt, one float64 Newton step;
+//                                       columns that lost all but 1e-12 of their norm to the
+//                                       projections are deflated to zero)
 //   3. P <- (P - Q C2) R1^-1, E = P^T P - I  (fused; per-row forward substitution, no inverse)
 //      P <- P (I - U(E)),  R2 = I + U(E)   with U(E) the upper triangle of E, halved diagonal: the
 //                                       Cholesky factor of I + E to first order, so P^T P = I up to

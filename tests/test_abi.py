@@ -67,6 +67,19 @@ def test_create_rejects_bad_arguments_before_any_device_work(libpath):
     st = L.svt_create(4, 5, 21, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, None, ctypes.byref(ctx))
     assert st == _abi.SVT_ERR_ARG
     assert b"nnz" in L.svt_last_error(None)
+    # option checks come before any device work too
+    opt = _abi.svt_options()
+    L.svt_default_options(ctypes.byref(opt))
+    assert opt.orth_grid == 0 and opt.lanczos_tol == 0.0
+    opt.orth_grid = -1
+    st = L.svt_create(4, 5, 3, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, ctypes.byref(opt),
+                      ctypes.byref(ctx))
+    assert st == _abi.SVT_ERR_ARG and b"orth_grid" in L.svt_last_error(None)
+    opt.orth_grid = 0
+    opt.precision = 7
+    st = L.svt_create(4, 5, 3, rows.ctypes.data, rows.ctypes.data, rows.ctypes.data, ctypes.byref(opt),
+                      ctypes.byref(ctx))
+    assert st == _abi.SVT_ERR_ARG and b"precision" in L.svt_last_error(None)
 
 
 def test_binding_struct_layouts_match_the_headers(tmp_path):
