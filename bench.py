@@ -1,19 +1,24 @@
 #!/usr/bin/env python
 """Benchmark of the SVT hot path on GB300: one step = one complete matrix-completion solve.
 
-Workload (default): 1000 x 1000, rank 10, |Omega| = 6 r (2n - r) = 119,400 sampled entries,
-N(0,1) planted factors, tau = 5n, delta = 1.2/p, eps = 1e-4, float32 values / float64 Lanczos
-basis and projected SVD (the single-solve configuration of the paper's Table 1, first row).
+Workload (default): 30000 x 30000, rank 10, |Omega| = 6 r (2n - r) = 3,599,400 sampled entries
+(0.4 % of 9e8 unknowns), N(0,1) planted factors, tau = 5n, delta = 1.2/p, eps = 1e-4 -- the last
+row of the paper's Table 1 -- with float64 values, sparse products, Lanczos basis and projected
+SVD (the paper's arithmetic: Matlab double).  Steps cycle over the instances of seeds 0-4 (Table 1
+averages five random instances); every instance counts, converged or not (k_max iterations).
 
 A step runs the whole path through the C-ABI: svt_create (Omega storage: CSR, CSC, permutation),
 svt_solve (kick with ||P_Omega M||_2, then Algorithm 1 until the relative residual on Omega is
-<= 1e-4) and svt_destroy.  `value` is SVT iterations per second over the timed steps (inputs
-resident in HBM); `e2e` is the same metric with the inputs copied from pinned host memory and the
-factors of X copied back inside every step.
+<= 1e-4 or k_max iterations) and svt_destroy.  `value` is SVT iterations per second over the timed
+steps (inputs resident in HBM); `e2e` is the same metric with the inputs copied from pinned host
+memory and the factors of X copied back inside every step (one pass over the seeds).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--config NAME] [--precision fp64|fp32] [--seeds 0,1,2,3,4] [--k-max 1000]
+    python bench.py --ncu-iters N ...   bounded run for a profiler: one create + kick + N
+                                        iterations of the first seed, nothing timed
 
-Under torchrun each rank solves its own problem (seed = --seed + rank): weak scaling, no data-path
+Under torchrun each rank solves its own problems (seed + 1000 rank): weak scaling, no data-path
 collective; the timing is the maximum over ranks.
 """
 from __future__ import annotations
@@ -167,81 +172,131 @@ def _barrier(dist):
         dist.barrier()
 
 
-class OracleIterations:
-    """The float64 oracle as it stands, run one SVT iteration at a time on the host cores: the kick
-    (||P_Omega M||_2 by the oracle's dense Jacobi SVD, k0 of eq. (5.3), Y^0 = k0 delta P_Omega M) is
-    set-up work, then every call of step() is one pass of Algorithm 1 (dense SVD of the iterate,
-    shrink, X on Omega, residual, dual step).  The oracle's iteration count to 1e-4 is ~1.01x its
-    number of dense SVDs, so the per-iteration rate stands for its whole-solve rate."""
-
-    def __init__(self, config_name, seed):
-        from oracle import svt as osvt
-        self.osvt = osvt
-        p = config_problem(config_name, seed)
-        self.p = p
-        self.rows = np.asarray(p.rows, dtype=np.int64)
-        self.cols = np.asarray(p.cols, dtype=np.int64)
-        self.m = np.asarray(p.vals, dtype=np.float64)
-        self.tau, self.delta = p.tau_default(), p.delta_default()
-        self.norm_m = float(np.sqrt(np.sum(self.m * self.m)))
-        norm2 = osvt.spectral_norm(p.n1, p.n2, self.rows, self.cols, self.m)
-        self.y = osvt.kick_k0(self.tau, self.delta, norm2) * self.delta * self.m
-        self.r_prev = 0
-        self.done = 0
-
-    def step(self):
-        st = self.osvt.svt_step(self.p.n1, self.p.n2, self.rows, self.cols, self.m, self.y, self.tau, self.r_prev, 5,
-                                self.norm_m)
-        self.r_prev = st.r_k
-        self.y = self.y + self.delta * st.e
-        self.done += 1
-        return st.res
-
-    def sample_text(self, n, seconds):
-        p = self.p
-        return ("SVT iterations %d..%d of the %dx%d rank-%d solve after the kick (kick untimed), float64 dense "
-                "one-sided Jacobi SVD per iteration, single thread, %.1f s timed"
-                % (self.done - n + 1, self.done, p.n1, p.n2, p.r, seconds))
+def _cpu_model():
+    """CPU model and core count of the host (lscpu where available)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    model = v
+                    break
+    except Exception:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return model, os.cpu_count() or 1
 
 
-def cpu_baseline(config_name, seed, max_iters=1):
-    """The float64 oracle on the host cores, on a bounded sample of the workload: `max_iters` SVT
-    iterations after the (untimed) kick."""
-    it = OracleIterations(config_name, seed)
-    t0 = time.perf_counter()
-    for _ in range(max_iters):
-        it.step()
-    dt = time.perf_counter() - t0
-    return {"value": max_iters / dt, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": it.sample_text(max_iters, dt), "seconds": dt}
+def _oracle_iterations(config_name, seed, first, count, threads):
+    """The float64 sparse-tier oracle (oracle/svt_sparse.py) as it stands, on the host cores: Algorithm 1
+    from the kick (||P_Omega M||_2 by the oracle's partial SVD, k0 of eq. (5.3)) through iteration
+    first + count - 1.  Returns the seconds of iterations first .. first + count - 1 (timed between the
+    per-iterate callbacks; the kick and earlier iterations are untimed set-up).  `threads` caps the
+    BLAS threads of the oracle's dense steps (its sparse products are single-threaded scipy)."""
+    code = r"""
+import json, sys, time
+sys.path.insert(0, %r)
+from oracle import svt_sparse
+from svt_inputs import config_problem
+p = config_problem(%r, %d)
+stamps = {}
+def cb(rec):
+    stamps[rec.k] = time.perf_counter()
+first, count = %d, %d
+svt_sparse.svt(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), k_max=first + count - 1,
+               keep_trace=False, on_iter=cb)
+ks = sorted(stamps)
+t0 = stamps[first - 1]
+t1 = stamps[ks[-1]]
+print(json.dumps({"seconds": t1 - t0, "iters": ks[-1] - (first - 1)}))
+""" % (ROOT, config_name, seed, first, count)
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out["seconds"], out["iters"]
+
+
+def cpu_baseline(config_name, seed):
+    """The float64 sparse-tier oracle on the host cores, on a bounded sample of the workload: SVT
+    iteration 2 of the instance (kick and iteration 1 untimed), with the BLAS threads at the core
+    count and again at one thread."""
+    model, cores = _cpu_model()
+    c = CONFIGS[config_name]
+    t_all, n_all = _oracle_iterations(config_name, seed, 2, 1, cores)
+    t_one, n_one = _oracle_iterations(config_name, seed, 2, 1, 1)
+    return {"value": n_all / t_all, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": "SVT iteration 2 of the %dx%d rank-%d instance of seed %d (kick and iteration 1 untimed), "
+                      "float64 sparse-tier oracle (scipy sparse products, block subspace iteration, Jacobi SVD), "
+                      "BLAS threads = %d, %.1f s timed" % (c["n1"], c["n2"], c["r"], seed, cores, t_all),
+            "cpu_model": model,
+            "single_thread": {"value": n_one / t_one, "unit": "iters/s", "cores": 1, "seconds": t_one}}
 
 
 def run_reference(args):
-    """The reference arm: the float64 oracle as it stands on the host cores, warm-up iterations
-    untimed, then `steps` timed SVT iterations.  Under torchrun only rank 0 runs it; the other ranks
-    exit without work (no process group is needed)."""
+    """The reference arm: the float64 oracle as it stands on the host cores.  Its kick and W warm-up
+    iterations are untimed; then `steps` SVT iterations are timed.  Under torchrun only rank 0 runs
+    it; the other ranks exit without work (no process group is needed)."""
     if int(os.environ.get("RANK", "0")) != 0:
         return 0
     c = CONFIGS[args.config]
-    it = OracleIterations(args.config, args.seed)
-    for _ in range(args.warmup):
-        it.step()
+    seed = args.seed_list[0]
+    model, cores = _cpu_model()
     steps = max(1, args.steps)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        it.step()
-    dt = time.perf_counter() - t0
-    v = steps / dt
-    sample = it.sample_text(steps, dt)
+    dt, n = _oracle_iterations(args.config, seed, 2 + args.warmup, steps, cores)
+    v = n / dt
+    p = config_problem(args.config, seed)
+    sample = ("SVT iterations %d..%d of the %dx%d rank-%d instance of seed %d (kick and earlier iterations "
+              "untimed), float64 sparse-tier oracle, BLAS threads = %d, %.1f s timed"
+              % (2 + args.warmup, 1 + args.warmup + n, c["n1"], c["n2"], c["r"], seed, cores, dt))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%s: %dx%d rank %d, |Omega|=%d" % (args.config, c["n1"], c["n2"], c["r"],
-                                                                        it.p.nnz),
-                       "step": "one SVT iteration of the float64 oracle (host cores)", "seed": args.seed},
-            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": _config_dict(args, p.nnz, 1),
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": model},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+    return 0
+
+
+def _config_dict(args, nnz, world):
+    c = CONFIGS[args.config]
+    return {"workload": "%s: %dx%d rank %d, |Omega|=%d (6 r(2n-r)), tau=5n, delta=1.2/p, eps=1e-4"
+                        % (args.config, c["n1"], c["n2"], c["r"], nnz),
+            "precision": "%s values and sparse products, float64 Lanczos basis and projected SVD"
+                         % ("float32" if args.precision == "fp32" else "float64"),
+            "step": "svt_create (Omega storage) + svt_solve (kick + iterations to 1e-4, at most k_max) + "
+                    "svt_destroy, one problem instance per step",
+            "seeds": args.seed_list, "k_max": args.k_max,
+            "l2": "inputs larger than L2 and a 256 MB buffer written between steps (flush)",
+            "parallelism": "replicas%d" % world}
+
+
+def run_ncu(args):
+    """Bounded run for a profiler: create, kick and `ncu_iters` SVT iterations of the first seed."""
+    import torch
+    from paper_0810_3286_gb300 import Solver, build
+    build.build()
+    torch.cuda.set_device(0)
+    p = config_problem(args.config, seed=args.seed_list[0])
+    with Solver(p.n1, p.n2, torch.from_numpy(p.rows).cuda(), torch.from_numpy(p.cols).cuda(),
+                torch.from_numpy(p.vals).cuda(), precision=args.precision) as s:
+        s.configure(p.tau_default(), p.delta_default(), 1e-4, 27)
+        k = 0
+        for k in range(args.ncu_iters):
+            if s.step()["stopped"]:
+                break
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_run": args.config, "precision": args.precision, "seed": args.seed_list[0],
+                          "iterations": k + 1, "counters": s.counters()}))
     return 0
 
 
@@ -255,48 +310,52 @@ def run_ours(args):
     from paper_0810_3286_gb300 import _abi
     stream = torch.cuda.current_stream()
 
-    p = config_problem(args.config, seed=args.seed + rank)
-    tau, delta = p.tau_default(), p.delta_default()
-    rows_d = torch.from_numpy(p.rows).to(device)
-    cols_d = torch.from_numpy(p.cols).to(device)
-    vals_d = torch.from_numpy(p.vals).to(device)
-    rows_h = torch.from_numpy(p.rows).pin_memory()
-    cols_h = torch.from_numpy(p.cols).pin_memory()
-    vals_h = torch.from_numpy(p.vals).pin_memory()
+    seeds = [sd + 1000 * rank for sd in args.seed_list]
+    probs = [config_problem(args.config, seed=sd) for sd in seeds]
+    dev_in = [(torch.from_numpy(p.rows).to(device), torch.from_numpy(p.cols).to(device),
+               torch.from_numpy(p.vals).to(device)) for p in probs]
+    host_in = [(torch.from_numpy(p.rows).pin_memory(), torch.from_numpy(p.cols).pin_memory(),
+                torch.from_numpy(p.vals).pin_memory()) for p in probs]
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > 129 MB L2
+    p0 = probs[0]
+    cap = 27
 
-    def step_device(profile_classes=()):
-        s = Solver(p.n1, p.n2, rows_d, cols_d, vals_d, precision=args.precision, stream=stream)
+    def step_device(i, profile_classes=(), k_max=None):
+        p = probs[i]
+        rows_d, cols_d, vals_d = dev_in[i]
+        s = Solver(p.n1, p.n2, rows_d, cols_d, vals_d, precision=args.precision, stream=stream,
+                   k_max=k_max or args.k_max)
         if profile_classes:
             s.set_profile(profile_classes)
-        res = s.solve(tau, delta, 1e-4, 27)
+        res = s.solve(p.tau_default(), p.delta_default(), 1e-4, cap, raise_on_nonconvergence=False)
         prof = s.profile() if profile_classes else None
         launches = s.kernel_launches()
         step_device.counters = s.counters()
         s.close()
         return res, launches, prof
 
-    U_h = torch.empty((p.n1, 27), dtype=torch.float64).pin_memory()
-    d_h = torch.empty(27, dtype=torch.float64).pin_memory()
-    V_h = torch.empty((p.n2, 27), dtype=torch.float64).pin_memory()
+    U_h = torch.empty((max(p.n1 for p in probs), cap), dtype=torch.float64).pin_memory()
+    d_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    V_h = torch.empty((max(p.n2 for p in probs), cap), dtype=torch.float64).pin_memory()
 
-    def step_e2e():
+    def step_e2e(i):
+        p = probs[i]
+        rows_h, cols_h, vals_h = host_in[i]
         s = Solver(p.n1, p.n2, rows_h.numpy(), cols_h.numpy(), vals_h.numpy(), precision=args.precision,
-                   stream=stream)
-        res = s.solve(tau, delta, 1e-4, 27)
+                   stream=stream, k_max=args.k_max)
+        res = s.solve(p.tau_default(), p.delta_default(), 1e-4, cap, raise_on_nonconvergence=False)
         r = res["rank"]
-        st = s._L.svt_get_factors(s._ctx, U_h.data_ptr(), d_h.data_ptr(), V_h.data_ptr(), 27)
+        st = s._L.svt_get_factors(s._ctx, U_h.data_ptr(), d_h.data_ptr(), V_h.data_ptr(), cap)
         assert st == 0
-        launches = s.kernel_launches()
         s.close()
-        return res, launches, r
+        return res, r
 
-    # --- warm-up ---
-    for _ in range(args.warmup):
-        step_device()
-    # --- per-class profile of one untimed solve: which kernel class dominates the device time ---
-    _, _, prof_all = step_device(tuple(_abi.PROF_CLASSES))
-    counters = dict(step_device.counters)
+    nseed = len(probs)
+    # --- warm-up: the same create / solve / destroy, capped at 30 iterations ---
+    for k in range(args.warmup):
+        step_device(k % nseed, k_max=30)
+    # --- per-class profile of one untimed solve (first 150 iterations of the first instance) ---
+    _, _, prof_all = step_device(0, tuple(_abi.PROF_CLASSES), k_max=min(args.k_max, 150))
     shares = {k: v[1] for k, v in prof_all.items()}
     tot = sum(shares.values()) or 1.0
     dominant_all = max(shares, key=lambda k: shares[k])
@@ -310,15 +369,17 @@ def run_ours(args):
     iters = 0
     launches = 0
     results = []
+    counters = []
     t_wall0 = time.perf_counter()
     for k in range(args.steps):
         l2_flush.zero_()
         ev[k][0].record(stream)
-        res, nl, _ = step_device()
+        res, nl, _ = step_device(k % nseed)
         ev[k][1].record(stream)
         iters += res["iterations"]
         launches += nl
         results.append(res)
+        counters.append(dict(step_device.counters))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     _barrier(dist)
@@ -329,37 +390,33 @@ def run_ours(args):
     iters_all = _sum_over_ranks(dist, float(iters), device)
     value = iters_all / total_s_max
 
-    # --- roofline pass: the same steps again with CUDA events (on the library's stream, recorded by
-    # the captured graphs) around every launch of every kernel class ---
+    # --- roofline pass: one solve per instance (at most 150 iterations each) with CUDA events (on the
+    # library's stream, recorded by the captured graphs) around every launch of every kernel class ---
     prof_timed = {}
-    roof_sweeps, roof_svd = 0.0, 0.0
-    for k in range(min(args.steps, 3)):
+    for i in range(nseed):
         l2_flush.zero_()
-        _, _, prof = step_device(tuple(_abi.PROF_CLASSES))
+        _, _, prof = step_device(i, tuple(_abi.PROF_CLASSES), k_max=min(args.k_max, 150))
         for c, (n, ms, by, fl) in prof.items():
             a = prof_timed.setdefault(c, [0, 0.0, 0.0, 0.0])
             a[0] += n; a[1] += ms; a[2] += by; a[3] += fl
-        roof_sweeps += step_device.counters["jacobi_sweeps"]
-        roof_svd += step_device.counters["svd_calls"]
     torch.cuda.synchronize()
 
-    # --- end to end through the C-ABI with host buffers ---
-    for _ in range(max(1, args.warmup // 2)):
-        step_e2e()
+    # --- end to end through the C-ABI with host buffers: one pass over the instances ---
+    step_e2e(0)
     _barrier(dist)
     torch.cuda.synchronize()
-    e2e_iters, e2e_r = 0, 0
-    t0 = time.perf_counter()
+    e2e_iters, e2e_bi, e2e_bo = 0, 0, 0
     e2e_ev = []
-    for k in range(args.steps):
+    for k in range(nseed):
         l2_flush.zero_()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        res, _, r = step_e2e()
+        res, r = step_e2e(k)
         b.record(stream)
         e2e_ev.append((a, b))
         e2e_iters += res["iterations"]
-        e2e_r = r
+        e2e_bi += probs[k].nnz * (4 + 4 + 8)
+        e2e_bo += 8 * (probs[k].n1 + probs[k].n2 + 1) * r
     torch.cuda.synchronize()
     e2e_s = sum(a.elapsed_time(b) for a, b in e2e_ev) / 1000.0
     e2e_s = _max_over_ranks(dist, e2e_s, device)
@@ -395,55 +452,49 @@ def run_ours(args):
                 "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
                 "algorithmic_flops_per_launch": flops_total / n_l if n_l else None}
 
-    # the projected SVD's float32 flops: per sweep (K - 1) rounds of K/2 pair rotations, each three
-    # length-K inner products (6K) and the rotation of two K-columns of G and of W (12K); K = J b
-    Kp = 3 * 16
-    jac_flops = roof_sweeps * (Kp - 1) * (Kp // 2) * 18.0 * Kp
     rooflines = {
         "orth": lambda: _roof_alu("orth", "k_orth_coop (block CGS2 + Cholesky QR, float64)", _sum(("orth",), 3),
                                   PEAK_FP64_TFLOPS, "float64"),
-        "jacobi": lambda: _roof_alu("jacobi", "k_jacobi_mixed (projected SVD, one CTA)", jac_flops,
-                                    PEAK_FP32_TFLOPS, "float32"),
         "spmm": lambda: _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)"),
         "spmm_t": lambda: _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)"),
         "sddmm_update": lambda: _roof(("sddmm_update",), "k_sddmm_update"),
     }
     timed_shares = {c: v[1] for c, v in prof_timed.items()}
     dominant = max(timed_shares, key=lambda c: timed_shares[c]) if timed_shares else "spmm"
-    roofline = rooflines.get(dominant, rooflines["spmm"])()
+    roofline = rooflines.get(dominant, rooflines["orth"])()
     roofline["time_share"] = timed_shares.get(dominant, 0.0) / (sum(timed_shares.values()) or 1.0)
-    roofline_spmm = _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)")
-    roofline_update = _roof(("sddmm_update",), "k_sddmm_update")
-    cpu = cpu_baseline(args.config, args.seed, max_iters=1) if not args.no_cpu_baseline else None
-    if cpu is not None:
-        cpu.pop("seconds", None)
-    c = CONFIGS[args.config]
-    mean_iters = float(np.mean([r["iterations"] for r in results]))
+    cpu = cpu_baseline(args.config, args.seed_list[0]) if not args.no_cpu_baseline else None
+    conv = [r for r in results if r["converged"]]
+    per_seed = {}
+    for k, r in enumerate(results):
+        sd = seeds[k % nseed]
+        e = per_seed.setdefault(str(sd), {"iterations": r["iterations"], "converged": bool(r["converged"]),
+                                          "ms": [], "rank": r["rank"], "residual": r["residual"]})
+        e["ms"].append(step_ms[k])
+    for e in per_seed.values():
+        e["ms"] = float(np.median(e["ms"]))
+    cnt = {k: float(np.mean([c[k] for c in counters])) for k in counters[0]} if counters else {}
     line = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total_s_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": "%s: %dx%d rank %d, |Omega|=%d (6 r(2n-r)), tau=5n, delta=1.2/p, eps=1e-4"
-                               % (args.config, c["n1"], c["n2"], c["r"], p.nnz),
-                   "precision": "%s values and sparse products, float64 Lanczos basis and projected SVD"
-                                % ("float32" if args.precision == "fp32" else "float64"),
-                   "step": "svt_create (Omega storage) + svt_solve (kick + iterations to 1e-4) + svt_destroy",
-                   "l2": "256 MB buffer written between steps (flush)", "parallelism": "replicas%d" % world,
-                   "seed": args.seed},
-        "time_to_1e-4_ms": 1000.0 * total_s_max / args.steps,
-        "iterations_per_solve": mean_iters, "k0": results[0]["k0"], "rank": results[0]["rank"],
-        "final_residual": results[-1]["residual"], "wall_s": t_wall,
+        "config": _config_dict(args, p0.nnz, world),
+        "time_to_1e-4_ms": (float(np.mean([step_ms[k] for k, r in enumerate(results) if r["converged"]]))
+                            if conv else None),
+        "converged_steps": len(conv), "per_seed": per_seed,
+        "iterations_per_solve": float(np.mean([r["iterations"] for r in results])),
+        "k0": results[0]["k0"], "wall_s": t_wall,
         "clocks": clk,
-        "e2e": {"value": e2e_iters / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": int(p.nnz * (4 + 4 + 8)),
-                "d2h_bytes_per_step": int(8 * (p.n1 + p.n2 + 1) * e2e_r)},
+        "e2e": {"value": e2e_iters / e2e_s, "unit": "iters/s", "h2d_bytes_per_step": int(e2e_bi / nseed),
+                "d2h_bytes_per_step": int(e2e_bo / nseed)},
         "gpu_launches": int(launches),
         "roofline": roofline,
-        "roofline_spmm": roofline_spmm,
-        "roofline_update": roofline_update,
+        "roofline_spmm": _roof(("spmm", "spmm_t"), "k_spmm (Y V and Y^T U)"),
+        "roofline_update": _roof(("sddmm_update",), "k_sddmm_update"),
         "kernel_time_shares": {k: round(v / tot, 4) for k, v in shares.items()},
         "dominant_kernel_class": dominant_all,
-        "solver_counters_per_solve": counters,
+        "solver_counters_per_solve": cnt,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -458,13 +509,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="single_1000", choices=sorted(CONFIGS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--config", default="large_30000", choices=sorted(CONFIGS))
+    ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64"])
+    ap.add_argument("--seeds", default="0,1,2,3,4",
+                    help="problem instances the steps cycle over (rank k solves seed + 1000 k)")
+    ap.add_argument("--k-max", type=int, default=1000, help="SVT iteration cap per solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--seed", type=int, default=0,
-                    help="problem seed of rank 0 (rank k solves seed + k); some 30000^2 instances, seed 0 among "
-                         "them, converge far more slowly than Table 1's average")
+    ap.add_argument("--ncu-iters", type=int, default=0,
+                    help="bounded run for a profiler: create + kick + this many iterations, nothing timed")
     args = ap.parse_args()
+    args.seed_list = [int(x) for x in args.seeds.split(",") if x.strip()]
+    if not args.seed_list:
+        ap.error("--seeds is empty")
+    if args.ncu_iters > 0:
+        return run_ncu(args)
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

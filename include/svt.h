@@ -93,6 +93,19 @@ typedef struct svt_options {
                              (the serving runtime) cap it so that their cooperative kernels are
                              resident together.  The row chunks of the Gram sums follow the grid,
                              so results are reproducible for a given value (not across values). */
+  double orth_repass;     /* orthonormality defect max |P^T P - I| of a block after its CGS2 + Cholesky QR pass
+                             above which the cooperative orthonormalisation repeats the whole pass on the result
+                             (Cholesky QR2; a block with nearly dependent columns loses orthogonality as
+                             cond(P)^2 eps in one pass); 0 = default 1e-6, < 0 = never */
+  /* Device allocator hook (both or neither; NULL = cudaMalloc / cudaFree): every device allocation
+   * of the context goes through device_alloc(bytes, alloc_user), which returns a device pointer
+   * aligned to 256 bytes or NULL when it cannot allocate (the call then fails with SVT_ERR_OOM and
+   * releases what it holds); device_free(ptr, alloc_user) is called only after the context's work on
+   * that memory has finished.  Lets a caller place the context in its own memory pool (a framework's
+   * caching allocator). */
+  void* (*device_alloc)(size_t bytes, void* alloc_user);
+  void (*device_free)(void* ptr, void* alloc_user);
+  void* alloc_user;
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
@@ -301,6 +314,16 @@ svt_status svt_sample_omega(int64_t m, int64_t n, int64_t nnz, uint64_t seed, in
 svt_status svt_save_state(svt_ctx* ctx, void* buf, size_t* bytes);
 svt_status svt_load_state(svt_ctx* ctx, const void* buf, size_t bytes);
 
+/*
+ * Failure injection for tests (the paper has no counterpart): the number of polls after which a
+ * grid-barrier wait in the context's cooperative kernels gives up (0 restores the default 2^22, far
+ * beyond any legitimate wait).  With a small value the barrier waits run out, the kernels return,
+ * and the call that issued them returns SVT_ERR_TIMEOUT with the context still usable: the barrier
+ * word is reset and the next shrink starts from a fresh block.  Synchronises the stream.
+ * Errors: SVT_ERR_ARG (NULL ctx, spins < 0).
+ */
+svt_status svt_set_barrier_spins(svt_ctx* ctx, int spins);
+
 /* Device kernels launched by this library so far on ctx (for launch accounting). */
 int64_t svt_kernel_launches(const svt_ctx* ctx);
 
@@ -325,11 +348,14 @@ svt_status svt_set_profile(svt_ctx* ctx, unsigned int class_mask);
 svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops);
 
 /*
- * Cumulative solver counters since svt_create, written to out[0 .. min(n, 8)):
+ * Cumulative solver counters since svt_create, written to out[0 .. min(n, 10)):
  *   [0] Lanczos cycles, [1] sparse products, [2] projected-SVD calls, [3] Jacobi sweeps in them,
  *   [4] basis columns deflated as numerically dependent, [5] largest orthonormality defect
- *   max |P^T P - I| seen after the Cholesky pass, [6] kernel launches, [7] shrinks whose Lanczos
- *   stagnated and were accepted at a relaxed tolerance (30x after 10 cycles, 300x after 25).
+ *   max |P^T P - I| of an accepted Cholesky pass (before the first-order corrections, which reduce
+ *   it to its square), [6] kernel launches, [7] shrinks whose Lanczos stagnated and were accepted
+ *   at a relaxed tolerance (30x after 10 cycles, 300x after 25), [8] block orthonormalisations
+ *   whose CGS2 + Cholesky QR pass was repeated (svt_options.orth_repass), [9] largest defect of
+ *   such a first pass.
  * Synchronises the stream.
  */
 svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);

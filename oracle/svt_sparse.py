@@ -26,7 +26,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import Callable, List, Optional
 
 import numpy as np
 import scipy.sparse as sp
@@ -125,8 +125,12 @@ class SparseSVTResult:
 
 
 def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: float = 1e-4, ell: int = 5,
-        k_max: int = 1000, k0: Optional[int] = None, keep_trace: bool = True, tol: float = 1e-12) -> SparseSVTResult:
-    """Algorithm 1 (Sec. 5.1.5) with the sparse shrink; the same records as the dense tier."""
+        k_max: int = 1000, k0: Optional[int] = None, keep_trace: bool = True, tol: float = 1e-12,
+        on_iter: Optional[Callable[[IterRecord], None]] = None) -> SparseSVTResult:
+    """Algorithm 1 (Sec. 5.1.5) with the sparse shrink; the same records as the dense tier.
+
+    on_iter, when given, receives every iterate's record as it is produced (x_omega and y_omega
+    included), so that long runs can be summarised without keeping the whole trace in memory."""
     rows = np.asarray(rows, dtype=np.int64)
     cols = np.asarray(cols, dtype=np.int64)
     m_vals = np.asarray(m_vals, dtype=np.float64)
@@ -148,9 +152,13 @@ def svt(n1: int, n2: int, rows, cols, m_vals, tau: float, delta: float, eps: flo
         x = np.einsum("pj,j,pj->p", U[rows], d, V[cols]) if r_k > 0 else np.zeros_like(y)
         e = m_vals - x
         res = math.sqrt(float(np.sum(e * e))) / norm_m
-        if keep_trace:
-            trace.append(IterRecord(k=k, s_k=s_k, passes=passes, r_k=r_k, res=res, x_omega=x.copy(),
-                                    y_omega=y.copy(), sigma=s[:r_k + ell].copy()))
+        if keep_trace or on_iter is not None:
+            rec = IterRecord(k=k, s_k=s_k, passes=passes, r_k=r_k, res=res, x_omega=x.copy(),
+                             y_omega=y.copy(), sigma=s[:r_k + ell].copy())
+            if keep_trace:
+                trace.append(rec)
+            if on_iter is not None:
+                on_iter(rec)
         r_prev = r_k
         if res <= eps:
             converged = True

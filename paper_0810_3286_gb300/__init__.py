@@ -72,7 +72,8 @@ class Solver:
     def __init__(self, m: int, n: int, rows, cols, m_vals, precision: str = "fp64", stream=None, ell: int = 5,
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
                  max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
-                 restart_steps: int = 0, bf16_switch: float = 1e-2, orth_grid: int = 0):
+                 restart_steps: int = 0, bf16_switch: float = 1e-2, orth_grid: int = 0, orth_repass: float = 0.0,
+                 allocator=None):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -89,6 +90,14 @@ class Solver:
         opt.restart_steps = int(restart_steps)
         opt.bf16_switch = float(bf16_switch)
         opt.orth_grid = int(orth_grid)
+        opt.orth_repass = float(orth_repass)
+        if allocator is not None:
+            # (alloc(bytes) -> int device pointer or 0, free(ptr)); the ctypes thunks must outlive
+            # the context
+            self._alloc_cbs = (_abi.ALLOC_FN(lambda nbytes, _u: int(allocator[0](nbytes)) or None),
+                               _abi.FREE_FN(lambda ptr, _u: allocator[1](ptr)))
+            opt.device_alloc = ctypes.cast(self._alloc_cbs[0], ctypes.c_void_p)
+            opt.device_free = ctypes.cast(self._alloc_cbs[1], ctypes.c_void_p)
         sh = _stream_handle(stream)
         opt.stream = sh
         on_device = hasattr(rows, "is_cuda") and rows.is_cuda
@@ -236,8 +245,9 @@ class Solver:
 
     def counters(self):
         """Cumulative solver counters (see svt_get_counters)."""
-        out = np.zeros(8)
-        _check(self._L.svt_get_counters(self._ctx, out.ctypes.data, 8), "svt_get_counters", self._ctx)
+        n = len(_abi.COUNTER_NAMES)
+        out = np.zeros(n)
+        _check(self._L.svt_get_counters(self._ctx, out.ctypes.data, n), "svt_get_counters", self._ctx)
         return dict(zip(_abi.COUNTER_NAMES, out.tolist()))
 
     def set_profile(self, classes=()):

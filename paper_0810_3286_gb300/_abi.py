@@ -52,6 +52,10 @@ class svt_options(ctypes.Structure):
         ("restart_steps", ctypes.c_int),
         ("bf16_switch", ctypes.c_double),
         ("orth_grid", ctypes.c_int),
+        ("orth_repass", ctypes.c_double),
+        ("device_alloc", ctypes.c_void_p),
+        ("device_free", ctypes.c_void_p),
+        ("alloc_user", ctypes.c_void_p),
     ]
 
 
@@ -85,6 +89,9 @@ class svt_result(ctypes.Structure):
 
 
 _vp = ctypes.c_void_p
+# svt_options.device_alloc / device_free
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _dp = ctypes.POINTER(ctypes.c_double)
 _ctxp = ctypes.c_void_p
@@ -188,13 +195,14 @@ PROTOTYPES = {
     "svt_set_noise_stop": (ctypes.c_int, [_ctxp, ctypes.c_double, ctypes.c_double]),
     "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, _vp]),
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
+    "svt_set_barrier_spins": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "svt_sddmm_update_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                                                 _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _dp, _vp]),
     "svt_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "deflated_columns",
-                 "max_orth_defect", "kernel_launches", "relaxed_shrinks"]
+                 "max_orth_defect", "kernel_launches", "relaxed_shrinks", "orth_repasses", "max_first_pass_defect"]
 
 # kernel classes of svt_set_profile / svt_get_profile
 PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update", "orth"]

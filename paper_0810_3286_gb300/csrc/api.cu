@@ -2,6 +2,7 @@
 // loop of Algorithm 1 (Sec. 5.1.5).  Host code here only orchestrates: every arithmetic step on
 // the matrices runs in the kernels of omega.cu, sparse.cu and dense.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,28 +29,13 @@ constexpr uint64_t kStateMagic = 0x5356545354415445ULL;  // "SVTSTATE"
 
 thread_local std::string g_create_error;
 
-// Temporary device buffers of one call, freed (after the stream drains) when the call returns.
-struct TmpBufs {
-  cudaStream_t st = nullptr;
-  std::vector<void*> ptrs;
-  explicit TmpBufs(cudaStream_t s) : st(s) {}
-  ~TmpBufs() {
-    if (ptrs.empty()) return;
-    cudaStreamSynchronize(st);
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <typename T>
-  bool get(T** p, size_t count) {
-    void* v = nullptr;
-    if (cudaMalloc(&v, count ? count * sizeof(T) : 16) != cudaSuccess) {
-      (void)cudaGetLastError();
-      *p = nullptr;
-      return false;
-    }
-    ptrs.push_back(v);
-    *p = (T*)v;
-    return true;
-  }
+// NVTX range over one host-side phase (visible in Nsight Systems; free when no tool is attached).
+// Device phases inside a replayed Lanczos-cycle graph are covered by the enclosing host range.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 }  // namespace
@@ -79,6 +65,7 @@ struct svt_ctx {
   void* Ybc[2] = {nullptr, nullptr};
   std::string last_error;
   std::vector<void*> allocations;
+
 
   // Omega
   int32_t *row_ptr = nullptr, *col_idx = nullptr, *col_ptr = nullptr, *row_idx = nullptr;
@@ -124,6 +111,8 @@ struct svt_ctx {
   double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
   double *Rkeep = nullptr, *scale = nullptr;
   bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
+  double orth_repass = 1e-6;              // defect above which a block's orthonormalisation pass is repeated
+  unsigned int barrier_spins = kBarrierSpinLimit;
   int coop_grid = 0;                      // > 0: orthonormalise each block in one cooperative kernel
   void* gbar = nullptr;                   // its grid barrier (8 bytes, zeroed)
   double* R2 = nullptr;                   // b x b product of the first correction and R1
@@ -182,17 +171,62 @@ static svt_status fail(svt_ctx* c, svt_status s, const char* fmt, ...) {
     if (s_ != SVT_OK) return s_;      \
   } while (0)
 
-static svt_status dalloc(svt_ctx* c, void** p, size_t bytes) {
-  *p = nullptr;
+// Device memory of a context: through the caller's allocator hook (svt_options.device_alloc /
+// device_free) when one is given, else cudaMalloc / cudaFree.  Memory is released only after the
+// context stream has drained.
+static void* dev_malloc(svt_ctx* c, size_t bytes) {
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e != cudaSuccess) {
+  void* p = nullptr;
+  if (c->opt.device_alloc) return c->opt.device_alloc(bytes, c->opt.alloc_user);
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
     (void)cudaGetLastError();
-    return fail(c, SVT_ERR_OOM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return nullptr;
   }
+  return p;
+}
+
+static void dev_free(svt_ctx* c, void* p) {
+  if (!p) return;
+  if (c->opt.device_free) c->opt.device_free(p, c->opt.alloc_user);
+  else cudaFree(p);
+}
+
+static svt_status dalloc(svt_ctx* c, void** p, size_t bytes) {
+  *p = dev_malloc(c, bytes);
+  if (!*p) return fail(c, SVT_ERR_OOM, "device allocation of %zu bytes failed", bytes);
   c->allocations.push_back(*p);
   return SVT_OK;
 }
+
+// Releases the most recent allocation of dalloc (call-local temporaries) after the stream drained.
+static void dfree_last(svt_ctx* c) {
+  if (c->allocations.empty()) return;
+  void* p = c->allocations.back();
+  c->allocations.pop_back();
+  dev_free(c, p);
+}
+
+namespace {
+// Temporary device buffers of one call, freed (after the stream drains) when the call returns.
+struct TmpBufs {
+  svt_ctx* c;
+  std::vector<void*> ptrs;
+  explicit TmpBufs(svt_ctx* cc) : c(cc) {}
+  ~TmpBufs() {
+    if (ptrs.empty()) return;
+    cudaStreamSynchronize(c->st);
+    for (void* p : ptrs) dev_free(c, p);
+  }
+  template <typename T>
+  bool get(T** p, size_t count) {
+    void* v = dev_malloc(c, count * sizeof(T));
+    *p = (T*)v;
+    if (!v) return false;
+    ptrs.push_back(v);
+    return true;
+  }
+};
+}  // namespace
 
 template <typename T>
 static svt_status dalloc_t(svt_ctx* c, T** p, size_t count) {
@@ -274,16 +308,21 @@ static svt_status sync_and_check(svt_ctx* c) {
   const unsigned int e = *herr;
   if (e) {
     CU(c, cudaMemsetAsync(c->err, 0, sizeof e, c->st));
-    if (e & SVT_DEVERR_INDEX_RANGE) return fail(c, SVT_ERR_ARG, "index outside [0,m) x [0,n)");
-    if (e & SVT_DEVERR_DUPLICATE) return fail(c, SVT_ERR_DUP_INDEX, "duplicate (row, col) pair in Omega");
-    if (e & SVT_DEVERR_NONFINITE) return fail(c, SVT_ERR_NUMERIC, "NaN or Inf in the residual");
-    if (e & SVT_DEVERR_CAPACITY) return fail(c, SVT_ERR_INTERNAL, "device buffer capacity exceeded");
-    if (e & SVT_DEVERR_JACOBI) return fail(c, SVT_ERR_NUMERIC, "projected Jacobi SVD did not converge");
+    // A grid barrier that gave up leaves arrivals counted in its word, and the basis it was
+    // orthonormalising half done (so other bits are often set in the same window): the word is
+    // zeroed first, whatever else is reported, so that the next cooperative launch starts from a
+    // clean barrier.  The Lanczos state is rebuilt by the next cycle (a fresh start block).
     if (e & SVT_DEVERR_BARRIER) {
-      // a cooperative kernel gave up at a grid barrier: reset it for later launches
       if (c->gbar) CU(c, cudaMemsetAsync(c->gbar, 0, 8, c->st));
+      CU(c, cudaStreamSynchronize(c->st));
+      c->warm_cols = 0;
       return fail(c, SVT_ERR_TIMEOUT, "a grid barrier of the cooperative orthonormalisation timed out");
     }
+    if (e & SVT_DEVERR_INDEX_RANGE) return fail(c, SVT_ERR_ARG, "index outside [0,m) x [0,n)");
+    if (e & SVT_DEVERR_DUPLICATE) return fail(c, SVT_ERR_DUP_INDEX, "duplicate (row, col) pair in Omega");
+    if (e & SVT_DEVERR_NONFINITE) return fail(c, SVT_ERR_NUMERIC, "NaN or Inf in a reduction (basis Gram or residual)");
+    if (e & SVT_DEVERR_CAPACITY) return fail(c, SVT_ERR_INTERNAL, "device buffer capacity exceeded");
+    if (e & SVT_DEVERR_JACOBI) return fail(c, SVT_ERR_NUMERIC, "projected Jacobi SVD did not converge");
     // SVT_DEVERR_CHOL is informational (deflation handled in-kernel)
   }
   return SVT_OK;
@@ -368,7 +407,8 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
     const double flops = per_row * (double)rows;
     l += prof_launch_f(c, SVT_PROF_ORTH, bytes, flops, [&] {
       return launch_orth_coop(P, Q, q_stride, nq, rows, b, c->gpart, c->G1, c->G2, c->G3, Tcol, Tdiag, kKMax, Pf,
-                              c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st);
+                              c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st,
+                              c->orth_repass, c->barrier_spins);
     });
     if (l == 0) return fail(c, SVT_ERR_CUDA, "cooperative orthonormalisation launch failed: %s",
                             cudaGetErrorString(cudaGetLastError()));
@@ -550,6 +590,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
 // One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
 static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, const double** theta_h,
                                 const double** res_h) {
+  NvtxRange nv("svt: Lanczos cycle (SpMM, reorthogonalisation, projected SVD)");
   if (c->opt.use_graphs) {
     TRY(run_cycle_graph(c, b, J, thick, Jprev));
   } else {
@@ -623,6 +664,8 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   for (int cyc = 0;; ++cyc) {
     const double *th, *rs;
     TRY(lanczos_cycle(c, b, J, thick, Jprev, &th, &rs));
+    if (!std::isfinite(th[0]) || !std::isfinite(rs[0]))
+      return fail(c, SVT_ERR_NUMERIC, "non-finite Ritz value or residual estimate");
     // stagnation: a cluster of Ritz values that the working precision cannot separate further
     // keeps its residuals above tol; after 10 cycles of one shrink the tolerance is relaxed 30x,
     // after 25 cycles 300x (recorded in the relaxed_shrinks counter)
@@ -690,6 +733,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
 
 // X = D_tau(Y): factors of the triplets with sigma > tau from the last cycle.
 static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out) {
+  NvtxRange nv("svt: shrink D_tau (rank-adaptive partial SVD, Ritz vectors)");
   std::vector<double> th;
   int s = 0, passes = 0, b = 0, J = 0;
   TRY(partial_svd(c, s_init, tau, th, &s, &passes, &b, &J));
@@ -747,6 +791,10 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->restart_steps = 0;
   opt->bf16_switch = 1e-2;
   opt->orth_grid = 0;
+  opt->orth_repass = 0.0;
+  opt->device_alloc = nullptr;
+  opt->device_free = nullptr;
+  opt->alloc_user = nullptr;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -766,7 +814,7 @@ extern "C" void svt_destroy(svt_ctx* c) {
     }
   }
   c->graphs.clear();
-  for (void* p : c->allocations) cudaFree(p);
+  for (void* p : c->allocations) dev_free(c, p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
   for (auto& r : c->prof_pending) {
     if (r.graph_owned) continue;
@@ -787,7 +835,7 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
   const long long nnz = c->nnz;
   int32_t *counts, *cursor, *scan_scratch, *src, *rows_csr, *maxseg;
   const long long nmax = std::max<long long>(m, n) + 1;
-  TmpBufs tmp(c->st);
+  TmpBufs tmp(c);
   if (!tmp.get(&counts, nmax) || !tmp.get(&cursor, nmax) || !tmp.get(&scan_scratch, scan_scratch_ints(nmax)) ||
       !tmp.get(&src, nnz) || !tmp.get(&rows_csr, nnz) || !tmp.get(&maxseg, 1))
     return fail(c, SVT_ERR_OOM, "device allocation of build scratch failed");
@@ -869,6 +917,7 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
   TRY(sync_and_check(c));
   double ss = 0.0;
   TRY(d2h_sync(c, &ss, c->dscal, sizeof ss));
+  if (!std::isfinite(ss)) return fail(c, SVT_ERR_ARG, "M_omega holds a NaN or Inf value");
   c->normF = std::sqrt(ss);
   return SVT_OK;
 }
@@ -876,6 +925,7 @@ static svt_status build_structure(svt_ctx* c, const int32_t* rows_d, const int32
 // Allocations, input staging and the Omega storage build of svt_create.  Local temporaries are
 // released when this returns, before svt_create destroys a failed context.
 static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* cols, const double* M_omega) {
+  NvtxRange nv("svt_create (Omega storage: CSR, CSC, permutations)");
   const int64_t m = c->m, n = c->n, nnz = c->nnz;
   StreamJoin join(c);
   TRY(dalloc_t(c, &c->err, 4));
@@ -941,7 +991,7 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   // inputs on the device
   const int32_t *rows_d = rows, *cols_d = cols;
   const double* M_d = M_omega;
-  TmpBufs staged(c->st);
+  TmpBufs staged(c);
   if (!c->opt.indices_on_device) {
     int32_t *r2, *c2;
     double* m2;
@@ -1003,6 +1053,9 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
     return fail(nullptr, SVT_ERR_ARG, "unknown precision");
   if (o.precision == SVT_BF16 && !(o.bf16_switch >= 0.0)) return fail(nullptr, SVT_ERR_ARG, "bf16_switch must be >= 0");
   if (o.orth_grid < 0) return fail(nullptr, SVT_ERR_ARG, "orth_grid must be >= 0");
+  if (!(o.orth_repass == o.orth_repass)) return fail(nullptr, SVT_ERR_ARG, "orth_repass is NaN");
+  if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
+    return fail(nullptr, SVT_ERR_ARG, "device_alloc and device_free must be given together");
   if (o.ell < 1) o.ell = 5;
   if (o.k_max < 1) o.k_max = 1000;
   if (o.lanczos_steps < 1) o.lanczos_steps = 3;
@@ -1015,6 +1068,7 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   c->prec = c->bf16_mode ? SVT_FP32 : o.precision;   // float32 values; the bfloat16 copies are extra
   c->vbytes = c->prec == SVT_FP64 ? 8 : 4;
   c->user_st = (cudaStream_t)o.stream;
+  c->orth_repass = o.orth_repass == 0.0 ? 1e-6 : (o.orth_repass < 0.0 ? 0.0 : o.orth_repass);
   svt_status s = SVT_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     s = fail(c, SVT_ERR_CUDA, "no CUDA device");
@@ -1042,6 +1096,7 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
 
 extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double eps, int max_rank, int64_t k0) {
   if (!c) return SVT_ERR_ARG;
+  NvtxRange nv("svt_configure (kick: ||P_Omega M||_2, k0, Y^0)");
   StreamJoin join(c);
   if (max_rank < 1 || max_rank > kMaxRankCap)
     return fail(c, SVT_ERR_ARG, "max_rank must be in [1, %d]", kMaxRankCap);
@@ -1118,12 +1173,14 @@ extern "C" svt_status svt_set_noise_stop(svt_ctx* c, double sigma, double eps_no
 
 extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   if (!c) return SVT_ERR_ARG;
+  NvtxRange nv("svt_step");
   StreamJoin join(c);
   if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
   CU(c, cudaEventRecord(c->ev0, c->st));
   int r = 0;
   TRY(shrink_current(c, c->tau, c->r + 1, &r));
   const int nxt = 1 - c->ycur;
+  NvtxRange nv_upd("svt: fused X on Omega + dual step + residual");
   SddmmDual dual{c->Yp[c->ycur], c->Ym[c->ycur], c->Yp[nxt], c->Ym[nxt], c->ds_E};
   const double upd_bytes = sddmm_bytes(c, r) + (c->ds_E > 0.0 ? 4.0 * c->nnz * c->vbytes - c->nnz * c->vbytes : 0.0);
   TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, upd_bytes, (2.0 * r + 4.0) * c->nnz, [&] {
@@ -1166,6 +1223,7 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
 
 extern "C" svt_status svt_solve(svt_ctx* c, double tau, double delta, double eps, int max_rank, svt_result* out) {
   if (!c) return SVT_ERR_ARG;
+  NvtxRange nv("svt_solve");
   StreamJoin join(c);
   cudaEvent_t e0, e1;
   CU(c, cudaEventCreate(&e0));
@@ -1236,8 +1294,7 @@ extern "C" svt_status svt_get_Y(svt_ctx* c, double* y) {
   TRY(launched(c, launch_store_values(c->prec, ycur_csr(c), tmp, c->nnz, c->st)));
   CU(c, cudaMemcpyAsync(y, tmp, sizeof(double) * c->nnz, cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaStreamSynchronize(c->st));
-  c->allocations.pop_back();
-  cudaFree(tmp);
+  dfree_last(c);
   return SVT_OK;
 }
 
@@ -1249,8 +1306,7 @@ extern "C" svt_status svt_set_Y(svt_ctx* c, const double* y) {
   CU(c, cudaMemcpyAsync(tmp, y, sizeof(double) * c->nnz, cudaMemcpyHostToDevice, c->st));
   TRY(launched(c, launch_load_values(c->prec, tmp, ycur_csr(c), ycur_csc(c), c->csr_to_csc, c->nnz, c->st)));
   CU(c, cudaStreamSynchronize(c->st));
-  c->allocations.pop_back();
-  cudaFree(tmp);
+  dfree_last(c);
   return SVT_OK;
 }
 
@@ -1496,13 +1552,38 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
     TRY(launched(c, launch_store_values(c->prec, ycur_csr(c), tmp, c->nnz, c->st)));
     TRY(launched(c, launch_gather_f64_to_f32(tmp, c->csc_to_csr, c->nnz, (float*)ycur_csc(c), c->st)));
     CU(c, cudaStreamSynchronize(c->st));
-    c->allocations.pop_back();
-    cudaFree(tmp);
+    dfree_last(c);
     if (c->bf16_active)
       TRY(launched(c, launch_to_bf16((const float*)ycur_csr(c), (const float*)ycur_csc(c), c->Yb[c->ycur],
                                      c->Ybc[c->ycur], c->nnz, c->st)));
   }
   return sync_and_check(c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Failure injection
+// ------------------------------------------------------------------------------------------------
+static void drop_graphs(svt_ctx* c) {
+  for (auto& g : c->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    for (auto& pn : g.prof) {
+      cudaEventDestroy(pn.a);
+      cudaEventDestroy(pn.b);
+    }
+  }
+  c->graphs.clear();
+}
+
+extern "C" svt_status svt_set_barrier_spins(svt_ctx* c, int spins) {
+  if (!c) return SVT_ERR_ARG;
+  if (spins < 0) return fail(c, SVT_ERR_ARG, "spins must be >= 0");
+  StreamJoin join(c);
+  CU(c, cudaStreamSynchronize(c->st));
+  prof_harvest(c);
+  // the limit is an argument of the captured kernels: later cycles are captured again
+  drop_graphs(c);
+  c->barrier_spins = spins > 0 ? (unsigned int)spins : kBarrierSpinLimit;
+  return SVT_OK;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1542,10 +1623,11 @@ extern "C" svt_status svt_get_counters(svt_ctx* c, double* out, int n) {
   unsigned long long dc[8] = {0};
   StreamJoin join(c);
   TRY(d2h_sync(c, dc, c->dcount, sizeof dc));
-  double maxdef = 0.0;
+  double maxdef = 0.0, maxdef1 = 0.0;
   std::memcpy(&maxdef, &dc[3], sizeof maxdef);
-  const double v[8] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],
-                       maxdef, (double)c->launches, (double)c->relaxed_shrinks};
-  for (int i = 0; i < n && i < 8; ++i) out[i] = v[i];
+  std::memcpy(&maxdef1, &dc[5], sizeof maxdef1);
+  const double v[10] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],
+                        maxdef, (double)c->launches, (double)c->relaxed_shrinks, (double)dc[4], maxdef1};
+  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
   return SVT_OK;
 }

@@ -37,11 +37,13 @@ __device__ __forceinline__ float warp_sum(float v) {
 // 2^31 and flips its top bit once, while no partial sum of the arrivals reaches it; a CTA waits
 // until the top bit differs from the one it saw on arrival.  One atomic per CTA, no reset between
 // barriers or launches.  The wait is bounded: after kBarrierSpinLimit polls (far beyond any
-// legitimate wait) the CTA records SVT_DEVERR_BARRIER and the call returns false; the caller then
-// returns from the kernel, and the host zeroes the word before the next launch.
+// legitimate wait; a smaller limit can be passed to exercise the path) the CTA records
+// SVT_DEVERR_BARRIER and the call returns false; the caller then returns from the kernel, and the
+// host zeroes the word before the next launch.
 static constexpr unsigned int kBarrierSpinLimit = 1u << 22;
 
-__device__ __forceinline__ bool svt_grid_barrier(unsigned int* word, unsigned int* err) {
+__device__ __forceinline__ bool svt_grid_barrier(unsigned int* word, unsigned int* err,
+                                                 unsigned int spin_limit = kBarrierSpinLimit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -53,7 +55,7 @@ __device__ __forceinline__ bool svt_grid_barrier(unsigned int* word, unsigned in
     volatile unsigned int* vw = word;
     unsigned int it = 0;
     while (((*vw ^ old) & 0x80000000u) == 0u) {
-      if (++it > kBarrierSpinLimit) {
+      if (++it > spin_limit) {
         ok = 0;
         svt_set_error(err, SVT_DEVERR_BARRIER);
         break;

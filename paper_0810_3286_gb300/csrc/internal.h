@@ -87,14 +87,17 @@ int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, d
 
 // The whole orthonormalisation above (gram, update + gram, Cholesky, update + gram, correction,
 // optionally the second correction) as one cooperative kernel with grid barriers.  bar: a zeroed
-// 8-byte barrier word (device).  Tcol / Tdiag / Pf may be NULL.  Uses at most
+// 8-byte barrier word (device).  Tcol / Tdiag / Pf may be NULL.  repass > 0: when the defect
+// max |P^T P - I| after the Cholesky pass exceeds it, the whole pass is repeated on its result and
+// the coefficients are composed (counters[4] += 1, counters[5] = max first-pass defect).
+// spin_limit: polls of a barrier wait before it gives up (SVT_DEVERR_BARRIER).  Uses at most
 // min(orth_coop_init(), max_grid) CTAs and at most gram_partial_doubles(n, nq, b) partials.
 // Returns 1 when launched, 0 when the device cannot run it (the caller then uses the sequence).
 int orth_coop_init();
 int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int n, int b, double* partial,
                      double* G1, double* G2, double* G3, double* Tcol, double* Tdiag, int ldT, float* Pf,
                      unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
-                     cudaStream_t st);
+                     cudaStream_t st, double repass, unsigned int spin_limit);
 
 // Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT): T = Xl diag(theta) Wr^T,
 // theta decreasing; Xl, Wr written K x K row-major.  Also res[i] = || S (Xl rows [K-b, K), column i) ||

@@ -526,7 +526,7 @@ int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, d
 // been written by other CTAs of the same kernel: read through L2.
 __device__ void reduce_entries(const double* __restrict__ partial, int nblk, int E, double* __restrict__ G,
                                const double* __restrict__ Gprev, double* __restrict__ Tcol, int ldT, int ncoef,
-                               int b) {
+                               int b, unsigned int* err = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int e = blockIdx.x * nw + warp; e < E; e += gridDim.x * nw) {
     double s = 0.0;
@@ -541,12 +541,39 @@ __device__ void reduce_entries(const double* __restrict__ partial, int nblk, int
     for (; k < nblk; k += 32) s += __ldcg(partial + (long long)k * E + e);
     s = warp_sum(s);
     if (lane == 0) {
+      if (err && !isfinite(s)) svt_set_error(err, SVT_DEVERR_NONFINITE);
       G[e] = s;
       if (Tcol && e < ncoef) {
         const int i = e / b, j = e - i * b;
         Tcol[i * ldT + j] = (Gprev ? __ldcg(Gprev + e) : 0.0) + s;
       }
     }
+  }
+}
+
+// Tdiag = A B for upper triangular b x b A, B in shared memory (the composed diagonal block of a
+// repeated pass).  All threads of one CTA.
+__device__ void compose_upper(const double* __restrict__ sA, const double* __restrict__ sB, int b,
+                              double* __restrict__ Tdiag, int ldT) {
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    double v = 0.0;
+    for (int k = i; k <= j; ++k) v += sA[i * b + k] * sB[k * b + j];
+    Tdiag[i * ldT + j] = v;
+  }
+}
+
+// Tcol += (C3 + C4) R1 with C3, C4 the coefficient rows (K x b) of the repeated pass in G1 / G2 and
+// R1 (upper triangular, shared memory) the first pass's factor: the first pass wrote Tcol = C1 + C2.
+// Entries spread over all threads of the grid; G1, G2 and Tcol were written by other CTAs of the
+// same kernel and are read through L2.
+__device__ void compose_coefs(const double* __restrict__ G1, const double* __restrict__ G2,
+                              const double* __restrict__ sR1, int K, int b, double* __restrict__ Tcol, int ldT) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K * b; e += gridDim.x * blockDim.x) {
+    const int i = e / b, j = e - i * b;
+    double v = 0.0;
+    for (int k = 0; k <= j; ++k) v += (__ldcg(G1 + i * b + k) + __ldcg(G2 + i * b + k)) * sR1[k * b + j];
+    Tcol[i * ldT + j] = __ldcg(Tcol + i * ldT + j) + v;
   }
 }
 
@@ -563,94 +590,173 @@ struct OrthCoopArgs {
   unsigned int* err;
   unsigned int* bar;          // grid barrier word
   int twoc;                   // second first-order correction
+  double repass;              // defect of the first pass above which the whole pass is repeated
+                              // (<= 0: never)
+  unsigned int spin_limit;    // polls of a barrier wait before it gives up
 };
 
 static constexpr size_t orth_coop_smem(int B) {
-  return (size_t)(OB_MAXK * B + 3 * B * B + B) * sizeof(double);
+  return (size_t)(OB_MAXK * B + 4 * B * B + B) * sizeof(double);
+}
+
+// max |E| over the live columns of U(E) in shared memory (the quantity correct_defect records),
+// returned to every lane of the calling warp.  Integer operations on the bit patterns.
+__device__ double defect_warp(const double* __restrict__ sU, int b) {
+  constexpr long long kAbs = 0x7FFFFFFFFFFFFFFFLL, kInf = 0x7FF0000000000000LL, kQuarter = 0x3FD0000000000000LL;
+  const int lane = threadIdx.x & 31;
+  long long off = 0, dia = 0;
+  for (int e = lane; e < b * b; e += 32) {
+    const int i = e / b, j = e - i * b;
+    if (j < i) continue;
+    const long long xi = __double_as_longlong(sU[i * b + i]), xj = __double_as_longlong(sU[j * b + j]);
+    const bool li = (xi >= 0 && xi <= kInf) || (xi & kAbs) < kQuarter;
+    const bool lj = (xj >= 0 && xj <= kInf) || (xj & kAbs) < kQuarter;
+    const long long x = __double_as_longlong(sU[e]) & kAbs;
+    if (li && lj && x <= kInf) {
+      if (i == j) dia = max(dia, x);
+      else off = max(off, x);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    off = max(off, __shfl_xor_sync(0xffffffffu, off, o));
+    dia = max(dia, __shfl_xor_sync(0xffffffffu, dia, o));
+  }
+  return fmax(__longlong_as_double(off), 2.0 * __longlong_as_double(dia));
 }
 
 #define SVT_BARRIER_OR_RETURN()                     \
   do {                                              \
-    if (!svt_grid_barrier(a.bar, a.err)) return;   \
+    if (!svt_grid_barrier(a.bar, a.err, a.spin_limit)) return;   \
   } while (0)
 
 template <int B>
 __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   extern __shared__ double sm_orth[];
   double* sC = sm_orth;                 // K x B coefficients (C1, then C2)
-  double* sR = sC + OB_MAXK * B;        // R1
+  double* sR = sC + OB_MAXK * B;        // R of the current pass
   double* sU = sR + B * B;              // U(E)
-  double* sR2 = sU + B * B;             // R1 diag(1 / diag(R1)); then (I + U(E)) R1 of a first correction
-  double* sD = sR2 + B * B;             // 1 / diag(R1)
+  double* sR2 = sU + B * B;             // R diag(1 / diag(R)); then (I + U(E)) R of a first correction
+  double* sD = sR2 + B * B;             // 1 / diag(R)
+  double* sR1 = sD + B;                 // R of the first pass, kept when the pass is repeated
+  __shared__ int s_repass;
   // a barrier of an earlier cooperative kernel gave up: the whole grid returns at once
   if (*(volatile unsigned int*)a.err & SVT_DEVERR_BARRIER) return;
   const int K = a.nq * B;
   const int nb = gridDim.x;
   const int r0 = blockIdx.x * a.rpc;
   const int r1 = min(a.n, r0 + a.rpc);
-  if (a.nq > 0) {
-    // C1 = Q^T P (with the diagonal of P^T P)
-    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, true);
-    SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, gram_entries(a.nq, B, true), a.G1, nullptr, nullptr, 0, 0, B);
-    SVT_BARRIER_OR_RETURN();
-    // P <- P - Q C1; [C2; A] = [Q, P]^T P; coefficients C1 + C2 -> Tcol
-    for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G1 + t);
+  const int step = ORTH_T / a.g;
+  // Pass 0 is block CGS2 + Cholesky QR.  When its result is far from orthonormal (a block with
+  // nearly dependent columns: Cholesky QR loses orthogonality as cond(P)^2 eps, and a column that
+  // lost most of its norm to the projections keeps components along Q of eps / (its norm ratio)),
+  // pass 1 repeats CGS2 + Cholesky QR on that result (the Cholesky QR2 remedy), and the
+  // coefficients compose: P_in = Q (C_a + C_b R_a) + P_out (R_b R_a).
+  for (int pass = 0; pass < 2; ++pass) {
+    if (a.nq > 0) {
+      // C1 = Q^T P (with the diagonal of P^T P)
+      gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, true);
+      SVT_BARRIER_OR_RETURN();
+      reduce_entries(a.partial, nb, gram_entries(a.nq, B, true), a.G1, nullptr, nullptr, 0, 0, B, a.err);
+      SVT_BARRIER_OR_RETURN();
+      // P <- P - Q C1; [C2; A] = [Q, P]^T P; coefficients C1 + C2 -> Tcol (first pass)
+      for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G1 + t);
+      __syncthreads();
+      update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1);
+      __syncthreads();
+      gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, false);
+      SVT_BARRIER_OR_RETURN();
+      reduce_entries(a.partial, nb, gram_entries(a.nq, B, false), a.G2, a.G1, pass == 0 ? a.Tcol : nullptr, a.ldT,
+                     K * B, B);
+      SVT_BARRIER_OR_RETURN();
+    } else {
+      gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
+      SVT_BARRIER_OR_RETURN();
+      reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G2, nullptr, nullptr, 0, 0, B, a.err);
+      SVT_BARRIER_OR_RETURN();
+    }
+    // R = chol(A) in every CTA, by warp 0, while warps 1.. project P <- P - Q C2; then
+    // P <- P R^-1 (forward substitution) by the whole CTA; E = P^T P - I
+    if (threadIdx.x < 32) {
+      // deflated columns are counted in the first pass (a repeated pass sees them again as zeros)
+      chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD,
+                   (blockIdx.x == 0 && pass == 0) ? a.counters : nullptr);
+    } else if (a.nq > 0) {
+      for (int t = threadIdx.x - 32; t < K * B; t += blockDim.x - 32) sC[t] = __ldcg(a.G2 + t);
+      asm volatile("bar.sync 1, %0;" ::"r"(ORTH_T - 32));   // warps 1.. only
+      update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1, 32, ORTH_T - 32);
+    }
     __syncthreads();
-    update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1);
+    for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR2[t] = sR[t] * sD[t % B];
     __syncthreads();
-    gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, false);
-    SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, gram_entries(a.nq, B, false), a.G2, a.G1, a.Tcol, a.ldT, K * B, B);
-    SVT_BARRIER_OR_RETURN();
-  } else {
+    update_rows(1, nullptr, 0, 0, nullptr, sR2, sD, a.P, B, a.g, r0, r1);
+    __syncthreads();
     gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
     SVT_BARRIER_OR_RETURN();
-    reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G2, nullptr, nullptr, 0, 0, B);
+    reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
     SVT_BARRIER_OR_RETURN();
-  }
-  // R1 = chol(A) in every CTA, by warp 0, while warps 1.. project P <- P - Q C2; then
-  // P <- P R1^-1 (forward substitution) by the whole CTA; E = P^T P - I
-  if (threadIdx.x < 32) {
-    chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD, blockIdx.x == 0 ? a.counters : nullptr);
-  } else if (a.nq > 0) {
-    for (int t = threadIdx.x - 32; t < K * B; t += blockDim.x - 32) sC[t] = __ldcg(a.G2 + t);
-    asm volatile("bar.sync 1, %0;" ::"r"(ORTH_T - 32));   // warps 1.. only
-    update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1, 32, ORTH_T - 32);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR2[t] = sR[t] * sD[t % B];
-  __syncthreads();
-  update_rows(1, nullptr, 0, 0, nullptr, sR2, sD, a.P, B, a.g, r0, r1);
-  __syncthreads();
-  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
-  SVT_BARRIER_OR_RETURN();
-  reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
-  SVT_BARRIER_OR_RETURN();
-  correct_load_U(a.G3, B, sU);
-  __syncthreads();
-  const int step = ORTH_T / a.g;
-  if (!a.twoc) {
-    // the coefficients by the last CTA, the defect by the last warp of CTA 0: off the rows'
-    // critical path where a CTA has fewer rows than warps
-    if (blockIdx.x == nb - 1) correct_coefs(sU, sR, B, a.Tdiag, a.ldT, nullptr, nullptr);
+    correct_load_U(a.G3, B, sU);
+    __syncthreads();
+    if (pass == 0 && a.repass > 0.0) {
+      // every CTA takes the same decision from the same G3
+      if (threadIdx.x < 32) {
+        const double d0 = defect_warp(sU, B);
+        if (threadIdx.x == 0) {
+          s_repass = d0 > a.repass ? 1 : 0;
+          if (s_repass && blockIdx.x == 0 && a.counters) {
+            atomicAdd(&a.counters[4], 1ull);
+            atomicMax(&a.counters[5], (unsigned long long)__double_as_longlong(d0));
+          }
+        }
+      }
+      __syncthreads();
+      if (s_repass) {
+        for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR1[t] = sR[t];
+        __syncthreads();
+        continue;
+      }
+    }
+    const bool second = pass == 1;
+    if (!a.twoc) {
+      // the coefficients by the last CTA, the defect by the last warp of CTA 0: off the rows'
+      // critical path where a CTA has fewer rows than warps
+      if (blockIdx.x == nb - 1) {
+        if (!second) {
+          correct_coefs(sU, sR, B, a.Tdiag, a.ldT, nullptr, nullptr);
+        } else if (a.Tdiag) {
+          correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2);
+          __syncthreads();
+          compose_upper(sR2, sR1, B, a.Tdiag, a.ldT);
+        }
+      }
+      if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
+      if (second && a.Tcol && a.nq > 0) compose_coefs(a.G1, a.G2, sR1, K, B, a.Tcol, a.ldT);
+      correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
+      return;
+    }
+    // two first-order corrections: P^T P = I up to O(|E|^4)
+    correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2);
     if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
+    correct_rows(sU, a.P, B, a.g, r0, r1, step, nullptr);
+    __syncthreads();
+    gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
+    SVT_BARRIER_OR_RETURN();
+    reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
+    SVT_BARRIER_OR_RETURN();
+    correct_load_U(a.G3, B, sU);
+    __syncthreads();
+    if (blockIdx.x == nb - 1) {
+      if (!second) {
+        correct_coefs(sU, sR2, B, a.Tdiag, a.ldT, nullptr, nullptr);
+      } else if (a.Tdiag) {
+        correct_coefs(sU, sR2, B, nullptr, 0, nullptr, sR);
+        __syncthreads();
+        compose_upper(sR, sR1, B, a.Tdiag, a.ldT);
+      }
+    }
+    if (second && a.Tcol && a.nq > 0) compose_coefs(a.G1, a.G2, sR1, K, B, a.Tcol, a.ldT);
     correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
     return;
   }
-  // two first-order corrections: P^T P = I up to O(|E|^4)
-  correct_coefs(sU, sR, B, nullptr, 0, nullptr, sR2);
-  if (blockIdx.x == 0 && a.counters && threadIdx.x >= ORTH_T - 32) correct_defect(sU, B, a.counters);
-  correct_rows(sU, a.P, B, a.g, r0, r1, step, nullptr);
-  __syncthreads();
-  gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
-  SVT_BARRIER_OR_RETURN();
-  reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G3, nullptr, nullptr, 0, 0, B);
-  SVT_BARRIER_OR_RETURN();
-  correct_load_U(a.G3, B, sU);
-  __syncthreads();
-  if (blockIdx.x == nb - 1) correct_coefs(sU, sR2, B, a.Tdiag, a.ldT, nullptr, nullptr);
-  correct_rows(sU, a.P, B, a.g, r0, r1, step, a.Pf);
 }
 
 #undef SVT_BARRIER_OR_RETURN
@@ -698,7 +804,7 @@ int orth_coop_init() {
 int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int n, int b, double* partial,
                      double* G1, double* G2, double* G3, double* Tcol, double* Tdiag, int ldT, float* Pf,
                      unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
-                     cudaStream_t st) {
+                     cudaStream_t st, double repass, unsigned int spin_limit) {
   const int gmax = std::min(orth_coop_init(), max_grid);
   if (gmax <= 0 || n <= 0) return 0;
   // at least GRAM_SUB rows per CTA, and at most gmax CTAs
@@ -709,6 +815,8 @@ int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int
   a.partial = partial; a.G1 = G1; a.G2 = G2; a.G3 = G3;
   a.Tcol = Tcol; a.Tdiag = Tdiag; a.ldT = ldT; a.Pf = Pf;
   a.counters = counters; a.err = err; a.bar = static_cast<unsigned int*>(bar); a.twoc = twoc;
+  a.repass = repass;
+  a.spin_limit = spin_limit;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(ORTH_T);

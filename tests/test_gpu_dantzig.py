@@ -40,7 +40,7 @@ def test_dantzig_parity_fp64_200(cuda):
     from paper_0810_3286_gb300 import Solver
     _, p, sigma = _noisy(200, 5, 11850, 0)
     tau = p.tau_default()
-    delta = 0.5 * p.n1 * p.n2 / p.nnz
+    delta = 0.5 * p.delta_default()   # 0.6 / p, half the paper's 1.2 / p (see above)
     ref = osvt.svt_dantzig(p.n1, p.n2, p.rows, p.cols, p.vals, sigma, tau, delta, eps=1e-4, k_max=40)
     s = Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision="fp64")
     s.set_dantzig(sigma)
