@@ -72,8 +72,9 @@ typedef struct svt_options {
   int k_max;              /* maximum SVT iterations after the kick (default 1000) */
   int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J*b <= 96) */
   int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
-  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-10 FP64, 1e-5 FP32 and
-                             BF16: ten times the rounding of the float32 sparse products) */
+  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-8 FP64: per-iterate agreement
+                             with a float64 SVT to ~1e-8; 1e-5 FP32 and BF16: ten times the rounding of the
+                             float32 sparse products) */
   int indices_on_device;  /* rows/cols/M_omega given to svt_create are device pointers */
   int use_graphs;         /* replay each Lanczos cycle as a captured CUDA graph (default 1) */
   uint64_t seed;          /* seed of the random start columns of the Lanczos blocks */
@@ -354,8 +355,9 @@ svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* 
  *   max |P^T P - I| of an accepted Cholesky pass (before the first-order corrections, which reduce
  *   it to its square), [6] kernel launches, [7] shrinks whose Lanczos stagnated and were accepted
  *   at a relaxed tolerance (30x after 10 cycles, 300x after 25), [8] block orthonormalisations
- *   whose CGS2 + Cholesky QR pass was repeated (svt_options.orth_repass), [9] largest defect of
- *   such a first pass.
+ *   whose CGS2 + Cholesky QR pass was repeated (a defect above svt_options.orth_repass, or
+ *   deflated columns replaced by fresh random directions), [9] largest defect of a first pass
+ *   that was repeated for its defect.
  * Synchronises the stream.
  */
 svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);

@@ -648,8 +648,10 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
                               int* passes_out, int* b_out, int* J_out, bool strict = false) {
   const int kmin = (int)std::min(c->m, c->n);
   // float32 values and products carry ~1e-6 of sigma_1 of rounding into the Lanczos relation
-  // (length-~100 float32 sums), so the float32 paths ask for ten times that
-  const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-10 : 1e-5);
+  // (length-~100 float32 sums), so the float32 paths ask for ten times that; the float64 path asks
+  // for 1e-8: its iterates then agree with the float64 oracle to ~1e-8 (the bound is 1e-5), and
+  // tighter tolerances stall on some 30000 x 30000 shrinks
+  const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-8 : 1e-5);
   int s = std::min(s_init, kmin);
   int passes = 1;
   int b = choose_block(c, s);
@@ -661,7 +663,11 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   const int max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
   bool thick = false;   // the next cycle is a thick restart of the previous one
   int Jprev = 0;        // block steps of the previous cycle
-  for (int cyc = 0;; ++cyc) {
+  // cycles of the current pass of the rank policy: each pass is a partial SVD of its own (Sec. 5.1.1
+  // asks the partial SVD for s_k triplets, then for s_k + l, ...), with its own cycle budget and
+  // stagnation clock
+  int cyc = 0;
+  for (;; ++cyc) {
     const double *th, *rs;
     TRY(lanczos_cycle(c, b, J, thick, Jprev, &th, &rs));
     if (!std::isfinite(th[0]) || !std::isfinite(rs[0]))
@@ -705,6 +711,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
         b = nb;
         J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
         TRY(set_start_block(c, b, std::min(c->warm_cols, b)));
+        cyc = -1;
         continue;
       }
       theta_out.assign(th, th + s_eff);

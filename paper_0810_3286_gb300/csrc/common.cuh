@@ -68,5 +68,15 @@ __device__ __forceinline__ bool svt_grid_barrier(unsigned int* word, unsigned in
   return s_ok != 0;
 }
 
+// Uniform(-1, 1) from output number index + 1 of SplitMix64 started at `seed` (Steele, Lea & Flood
+// 2014): the random start columns of the Lanczos blocks and fresh directions for deflated ones.
+__device__ __forceinline__ double svt_uniform_pm1(unsigned long long seed, unsigned long long index) {
+  unsigned long long z = seed + (index + 1ULL) * 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
 static inline int svt_ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 static inline long long svt_min_ll(long long a, long long b) { return a < b ? a : b; }

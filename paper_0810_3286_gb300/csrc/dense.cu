@@ -60,11 +60,7 @@ __global__ void k_random_block(double* __restrict__ P, int n, int b, int c0, uns
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     int c = (int)(e % b);
     if (c < c0) continue;
-    unsigned long long z = seed + ((unsigned long long)e + 1ULL) * 0x9e3779b97f4a7c15ULL;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    z ^= z >> 31;
-    P[e] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    P[e] = svt_uniform_pm1(seed, (unsigned long long)e);
   }
 }
 

@@ -99,7 +99,8 @@ template <typename R>
 __device__ __forceinline__ R shfl_grp(R v, int o) { return shfl_xor_r(v, o); }
 
 template <typename R, int JR, bool ACC>   // JR = rows per lane = ceil(K / JL), a compile-time bound
-__device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag) {
+__device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag,
+                             bool quad_stop = false) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gl = lane & (JL - 1);                 // lane inside the pair group
   const int gsub = lane / JL;                     // pair slot inside the warp
@@ -179,8 +180,10 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
     for (int w = 0; w < nw; ++w) sweep_max = fmaxf(sweep_max, warp_max[w]);
     if (!*flag || final_sweep) break;
     // quadratic convergence: once every rotated pair had |cos| <= sqrt(tol), the next sweep leaves
-    // them at the tol level, so it is the last one (no further verification sweep)
+    // them at the tol level, so it is the last one (no further verification sweep); with quad_stop
+    // the sweep that rotated them is already the last
     final_sweep = sweep_max <= (float)sqrt(tol);
+    if (quad_stop && final_sweep) break;
     __syncthreads();
   }
   return sweep + 1;
@@ -215,29 +218,115 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 // ------------------------------------------------------------------------------------------------
 // float64 path
 // ------------------------------------------------------------------------------------------------
+// float64 path in two phases.  One float64 rotation costs ~20 dependent float64 operations and its
+// column updates run on the float64 pipe (2 FMA per clock per SM on GB300), so full float64 sweeps
+// from T take milliseconds.  Instead:
+//   A. float32 sweeps on the columns of T with the rotations accumulated in W (float32): this
+//      converges the angles to the float32 level (|cos| ~ 1e-6);
+//   B. in float64: W <- W (I - (W^T W - I) / 2) (one first-order step back to orthonormality,
+//      1e-12), G = T W, and float64 sweeps on (G, W) from there: quadratic convergence takes the
+//      float32-level angles to the float64 tolerance in two sweeps.
+// The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
 template <int JR>
 __global__ void __launch_bounds__(512)
 k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
              double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
              double tol, int max_sweeps, unsigned int* err, unsigned long long* counters) {
   extern __shared__ double sm64[];
-  double* G = sm64;                   // K x K column-major
-  double* W = G + K * K;              // K x K column-major
-  double* nrm = W + K * K;            // K
+  double* W = sm64;                   // K x K column-major: the accumulated rotations (float64, phase B)
+  double* G = W + K * K;              // K x K column-major: T W (phase B); phase A keeps its float32
+                                      // G32 and W32 here
+  double* nrm = G + K * K;            // K
   double* rnrm = nrm + K;             // K: 1 / nrm (0 for a zero column)
   int* order = (int*)(rnrm + K);      // K
   unsigned char* sched = (unsigned char*)(order + K);
   __shared__ int flag;
+  float* G32 = (float*)G;
+  float* W32 = G32 + K * K;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int i = e / K, c = e - i * K;
-    G[c * K + i] = T[i * ldT + c];
-    W[c * K + i] = (i == c) ? 1.0 : 0.0;
+    G32[c * K + i] = (float)T[i * ldT + c];
+    W32[c * K + i] = (i == c) ? 1.f : 0.f;
   }
   build_schedule(sched, K);
   __syncthreads();
-  const int sweeps = jacobi_sweeps<double, JR, true>(G, W, sched, K, tol, max_sweeps, &flag);
+  // A. float32 sweeps (the float32 rounding level of the angles)
+  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) W[e] = (double)W32[e];
+  __syncthreads();
+  // B1. E = W^T W - I (upper triangle, into G), then W <- W (I - E / 2) row by row (a row of the
+  // new W needs only the same row of the old one)
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int p = e / K, q = e - p * K;
+    if (q < p) continue;
+    const double* wp = W + p * K;
+    const double* wq = W + q * K;
+    double s0 = 0.0, s1 = 0.0;
+    int i = 0;
+    for (; i + 1 < K; i += 2) {
+      s0 += wp[i] * wq[i];
+      s1 += wp[i + 1] * wq[i + 1];
+    }
+    if (i < K) s0 += wp[i] * wq[i];
+    const double v = (s0 + s1) - (p == q ? 1.0 : 0.0);
+    G[q * K + p] = v;
+    G[p * K + q] = v;
+  }
+  __syncthreads();
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < K; i += nw) {
+      double wi[(JMAXK + 31) / 32];
+#pragma unroll
+      for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
+        const int c = lane + 32 * t;
+        wi[t] = c < K ? W[c * K + i] : 0.0;
+      }
+      double out[(JMAXK + 31) / 32];
+#pragma unroll
+      for (int t = 0; t < (JMAXK + 31) / 32; ++t) out[t] = wi[t];
+#pragma unroll
+      for (int tk = 0; tk < (JMAXK + 31) / 32; ++tk) {
+        for (int kk = 0; kk < 32; ++kk) {
+          const int k = 32 * tk + kk;
+          const double wk = __shfl_sync(0xffffffffu, wi[tk], kk);   // W[i, k], held by lane kk
+          if (k >= K) break;                                         // warp-uniform
+#pragma unroll
+          for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
+            const int c = lane + 32 * t;
+            if (c < K) out[t] = fma(-0.5 * wk, G[c * K + k], out[t]);
+          }
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
+        const int c = lane + 32 * t;
+        if (c < K) W[c * K + i] = out[t];
+      }
+    }
+  }
+  __syncthreads();
+  // B2. G = T W (T block upper triangular: row i has no entries left of its diagonal block)
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int c = e / K, i = e - c * K;
+    const double* trow = T + (long long)i * ldT;
+    const double* wc = W + c * K;
+    double s0 = 0.0, s1 = 0.0;
+    int k = (i / b) * b;
+    for (; k + 1 < K; k += 2) {
+      s0 += trow[k] * wc[k];
+      s1 += trow[k + 1] * wc[k + 1];
+    }
+    if (k < K) s0 += trow[k] * wc[k];
+    G[c * K + i] = s0 + s1;
+  }
+  __syncthreads();
+  // B3. float64 sweeps from the float32-level angles
+  const int sweeps_b = jacobi_sweeps<double, JR, true>(G, W, sched, K, tol, max_sweeps, &flag, true);
+  const int sweeps = sweeps_a + sweeps_b;
   if (threadIdx.x == 0) {
-    if (sweeps > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
+    if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
     if (counters) {
       atomicAdd(&counters[0], 1ULL);
       atomicAdd(&counters[1], (unsigned long long)sweeps);

@@ -689,6 +689,29 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
     for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR2[t] = sR[t] * sD[t % B];
     __syncthreads();
     update_rows(1, nullptr, 0, 0, nullptr, sR2, sD, a.P, B, a.g, r0, r1);
+    if (pass == 0 && a.repass > 0.0) {
+      // Deflated columns (zero rows of R: numerically dependent on Q and on the block's other
+      // columns) are replaced by fresh random directions, and the pass is repeated to make them
+      // orthonormal to Q and to the rest of the block: the block keeps its width, so the Krylov
+      // space keeps growing (block Lanczos breakdown).  A deflated column has no coefficient in
+      // P_in = Q C_a + P R_a, so the relation still holds.  The seed comes from R, identical in
+      // every CTA and different from block to block.
+      int ndef = 0;
+      for (int j = 0; j < B; ++j) ndef += sD[j] == 0.0 ? 1 : 0;
+      if (ndef > 0) {
+        __syncthreads();   // the substitution above wrote these rows
+        const unsigned long long seed =
+            (unsigned long long)__double_as_longlong(sR[0]) ^ ((unsigned long long)a.nq << 40) ^ (unsigned long long)a.n;
+        for (int e = threadIdx.x; e < (r1 - r0) * B; e += blockDim.x) {
+          const int i = r0 + e / B, j = e - (e / B) * B;
+          if (sD[j] == 0.0) a.P[(long long)i * B + j] = svt_uniform_pm1(seed, (unsigned long long)i * B + j);
+        }
+        for (int t = threadIdx.x; t < B * B; t += blockDim.x) sR1[t] = sR[t];
+        if (threadIdx.x == 0 && blockIdx.x == 0 && a.counters) atomicAdd(&a.counters[4], 1ull);
+        __syncthreads();
+        continue;
+      }
+    }
     __syncthreads();
     gram_chunk(nullptr, 0, 0, a.P, B, r0, r1, a.partial, false);
     SVT_BARRIER_OR_RETURN();

@@ -2,6 +2,8 @@
 
 Usage:  python tests/golden/make_tierb_trace.py <workload> <seed> [k_max]
         (workload names as in svt_inputs.CONFIGS, e.g. single_10000 4)
+        python tests/golden/make_tierb_trace.py --thin <trace file>
+        (keeps the sampled values of every 10th iterate and of the last one only)
 
 Runs Algorithm 1 (Sec. 5.1.5) with the oracle's sparse shrink (oracle/svt_sparse.py: block
 subspace iteration with Rayleigh-Ritz through the oracle's Jacobi SVD, Ritz residuals <= 1e-12
@@ -14,10 +16,11 @@ oracle/ and the input generator are called.  The output file
 holds a header (sizes, parameters, k0 of eq. (5.3), ||P_Omega M||_2, and 64 positions of Omega in
 row-major order, drawn by a fixed PCG64 stream) and one line per iterate:
 
-    k  r_k  s_k  passes  residual  x_1 .. x_64
+    k  r_k  s_k  passes  residual  [x_1 .. x_64]
 
-with x_i = X^k at the i-th sampled position.  Lines are flushed as they are produced, so a run
-that is stopped early leaves a valid prefix.
+with x_i = X^k at the i-th sampled position (every iterate as written; --thin keeps them on every
+10th iterate and the last one).  Lines are flushed as they are produced, so a run that is stopped
+early leaves a valid prefix.
 """
 from __future__ import annotations
 
@@ -48,7 +51,26 @@ def trace_path(workload: str, seed: int) -> str:
     return os.path.join(HERE, "tierb_trace_%s_seed%d.txt" % (workload, seed))
 
 
+def thin(path: str, every: int = 10) -> None:
+    """Rewrites a trace keeping the sampled X values of every `every`-th iterate and of the last."""
+    with open(path) as f:
+        lines = f.readlines()
+    data = [i for i, ln in enumerate(lines) if ln.strip() and not ln.startswith("#")]
+    last = data[-1] if data else -1
+    out = []
+    for i, ln in enumerate(lines):
+        if i in data and i != last and int(ln.split()[0]) % every != 0:
+            ln = " ".join(ln.split()[:5]) + "\n"
+        out.append(ln)
+    with open(path + ".tmp", "w") as f:
+        f.writelines(out)
+    os.replace(path + ".tmp", path)
+
+
 def main(argv) -> int:
+    if argv[1] == "--thin":
+        thin(argv[2])
+        return 0
     workload, seed = argv[1], int(argv[2])
     k_max = int(argv[3]) if len(argv) > 3 else 400
     p = config_problem(workload, seed)
@@ -80,7 +102,7 @@ def main(argv) -> int:
 
 
 def read_trace(path: str):
-    """(header dict, positions, rows) with rows = list of (k, r_k, s_k, passes, res, x_sample)."""
+    """(header dict, positions, rows) with rows = list of (k, r_k, s_k, passes, res, x_sample or None)."""
     head, pos, rows = {}, None, []
     with open(path) as f:
         for line in f:
@@ -95,7 +117,7 @@ def read_trace(path: str):
             elif line.strip():
                 t = line.split()
                 rows.append((int(t[0]), int(t[1]), int(t[2]), int(t[3]), float(t[4]),
-                             np.array([float(v) for v in t[5:]])))
+                             np.array([float(v) for v in t[5:]]) if len(t) > 5 else None))
     return head, pos, rows
 
 
