@@ -57,6 +57,17 @@ typedef enum svt_status {
  * dual step).  The Lanczos basis, its reorthogonalisation and the projected SVD that fixes the
  * singular values compared against tau are float64 in every mode. */
 enum { SVT_FP64 = 0, SVT_FP32 = 1, SVT_BF16 = 2 };
+/* Shrink engines (svt_options.shrink_engine).  SVT_SHRINK_LANCZOS: the rank-adaptive block
+ * Lanczos partial SVD (Sec. 5.1.1).  SVT_SHRINK_RANDOMIZED: the first alternative of Sec. 6, a
+ * randomized range finder: with l = min(32, s_k + rsvd_oversample rounded up to a multiple of 8)
+ * test columns Omega (the previous shrink's right singular vectors, then uniform(-1, 1) columns:
+ * element (i, c) of the n x l block is (SplitMix64 output number i l + c + 1 at seed
+ * rsvd_seed + 1000 k + pass) >> 11 times 2^-52, minus 1, k the SVT iteration and pass the rank
+ * policy's pass counted from 0), Q = orth(Y Omega), rsvd_power steps Q <- orth(Y orth(Y^T Q)),
+ * then D_tau(Q Q^T Y) from the SVD of Q^T Y; the rank policy of Sec. 5.1.1 sets s_k.  Exact when
+ * l >= rank(Y); otherwise an approximation of D_tau(Y) (the paper leaves its accuracy open).
+ * Needs min(m, n) >= 32 and s_k + rsvd_oversample <= 32 (else SVT_ERR_RANK_LIMIT). */
+enum { SVT_SHRINK_LANCZOS = 0, SVT_SHRINK_RANDOMIZED = 1 };
 /* SVT_BF16: float32 values and dual iterate as SVT_FP32, plus bfloat16 copies of Y (written by the
  * fused update) that the sparse products read, with float32 accumulation, while the relative
  * residual of eq. (5.5) is at or above svt_options.bf16_switch; once it falls below, the products
@@ -107,6 +118,10 @@ typedef struct svt_options {
   void* (*device_alloc)(size_t bytes, void* alloc_user);
   void (*device_free)(void* ptr, void* alloc_user);
   void* alloc_user;
+  int shrink_engine;      /* SVT_SHRINK_LANCZOS (default) or SVT_SHRINK_RANDOMIZED */
+  int rsvd_oversample;    /* randomized engine: test columns beyond s_k (default 8, 1 .. 24) */
+  int rsvd_power;         /* randomized engine: power steps (default 1, 0 .. 8) */
+  uint64_t rsvd_seed;     /* randomized engine: base seed of the random test columns (default 0) */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
@@ -233,6 +248,26 @@ svt_status svt_step(svt_ctx* ctx, svt_step_info* info);
  * first error of a step.  out may be NULL.
  */
 svt_status svt_solve(svt_ctx* ctx, double tau, double delta, double eps, int max_rank, svt_result* out);
+
+/*
+ * Continuation (Sec. 6): the problem for a larger tau is started from the solution for the previous
+ * tau.  svt_set_tau changes tau for the following svt_step calls and keeps the dual iterate Y, the
+ * factors of X^k, the rank and the warm start; the iteration count restarts at 0.
+ * Errors: SVT_ERR_ARG (NULL ctx, tau not positive and finite, context not configured).
+ */
+svt_status svt_set_tau(svt_ctx* ctx, double tau);
+
+/*
+ * Continuation in full: svt_configure(ctx, taus[0], delta, eps, max_rank, -1) (the kick of eq. (5.3)
+ * at taus[0]), then for i = 0 .. n_tau - 1: tau = taus[i] (svt_set_tau from the second stage on) and
+ * svt_step until the stopping rule eq. (5.5) holds (at most k_max steps per stage).  Each stage
+ * starts from the dual iterate at which the previous one stopped.  stage_iters (n_tau entries, may
+ * be NULL) receives each stage's iterations; out (may be NULL) the totals, with iterations summed
+ * over the stages.  Returns SVT_OK when the last stage met the stopping rule,
+ * SVT_ERR_NOT_CONVERGED when a stage ran k_max steps, or the first error of a step.
+ */
+svt_status svt_solve_continuation(svt_ctx* ctx, const double* taus, int n_tau, double delta, double eps,
+                                  int max_rank, int64_t* stage_iters, svt_result* out);
 
 /* Rank r of the current X^k (0 before the first step). */
 svt_status svt_get_rank(const svt_ctx* ctx, int* r);

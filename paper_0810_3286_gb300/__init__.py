@@ -73,7 +73,8 @@ class Solver:
                  k_max: int = 1000, lanczos_steps: int = 3, lanczos_tol: float = 0.0, seed: int = 0x5EED5EED,
                  max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
                  restart_steps: int = 0, bf16_switch: float = 1e-2, orth_grid: int = 0, orth_repass: float = 0.0,
-                 allocator=None):
+                 allocator=None, shrink_engine: str = "lanczos", rsvd_oversample: int = 8, rsvd_power: int = 1,
+                 rsvd_seed: int = 0):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -91,6 +92,10 @@ class Solver:
         opt.bf16_switch = float(bf16_switch)
         opt.orth_grid = int(orth_grid)
         opt.orth_repass = float(orth_repass)
+        opt.shrink_engine = {"lanczos": _abi.SVT_SHRINK_LANCZOS, "randomized": _abi.SVT_SHRINK_RANDOMIZED}[shrink_engine]
+        opt.rsvd_oversample = int(rsvd_oversample)
+        opt.rsvd_power = int(rsvd_power)
+        opt.rsvd_seed = int(rsvd_seed) & (2**64 - 1)
         if allocator is not None:
             # (alloc(bytes) -> int device pointer or 0, free(ptr)); the ctypes thunks must outlive
             # the context
@@ -171,6 +176,23 @@ class Solver:
         allow = () if raise_on_nonconvergence else (SVT_ERR_NOT_CONVERGED,)
         _check(st, "svt_solve", self._ctx, allow=allow)
         return SolveResult({f: getattr(res, f) for f, _ in svt_result._fields_})
+
+    def set_tau(self, tau: float):
+        """Continuation (Sec. 6): tau for the following steps, keeping Y, X and the warm start."""
+        _check(self._L.svt_set_tau(self._ctx, tau), "svt_set_tau", self._ctx)
+
+    def solve_continuation(self, taus, delta: float = 0.0, eps: float = 1e-4, max_rank: int = 27,
+                           raise_on_nonconvergence: bool = True):
+        """Algorithm 1 at taus[0] (with the kick), then at each later tau from the previous stage's
+        dual iterate (Sec. 6).  Returns (SolveResult, per-stage iterations)."""
+        t = np.ascontiguousarray(taus, dtype=np.float64)
+        stages = np.zeros(t.shape[0], dtype=np.int64)
+        res = svt_result()
+        st = self._L.svt_solve_continuation(self._ctx, t.ctypes.data, int(t.shape[0]), delta, eps, max_rank,
+                                            stages.ctypes.data, ctypes.byref(res))
+        allow = () if raise_on_nonconvergence else (SVT_ERR_NOT_CONVERGED,)
+        _check(st, "svt_solve_continuation", self._ctx, allow=allow)
+        return SolveResult({f: getattr(res, f) for f, _ in svt_result._fields_}), stages.tolist()
 
     def shrink(self, tau: float = 0.0):
         """D_tau of the current Y; returns (rank, singular values > tau)."""

@@ -34,6 +34,9 @@ SVT_FP64 = 0
 SVT_FP32 = 1
 SVT_BF16 = 2
 
+SVT_SHRINK_LANCZOS = 0
+SVT_SHRINK_RANDOMIZED = 1
+
 
 class svt_options(ctypes.Structure):
     _fields_ = [
@@ -56,6 +59,10 @@ class svt_options(ctypes.Structure):
         ("device_alloc", ctypes.c_void_p),
         ("device_free", ctypes.c_void_p),
         ("alloc_user", ctypes.c_void_p),
+        ("shrink_engine", ctypes.c_int),
+        ("rsvd_oversample", ctypes.c_int),
+        ("rsvd_power", ctypes.c_int),
+        ("rsvd_seed", ctypes.c_uint64),
     ]
 
 
@@ -196,6 +203,9 @@ PROTOTYPES = {
     "svt_get_profile": (ctypes.c_int, [_ctxp, _vp, _vp, _vp, _vp]),
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
     "svt_set_barrier_spins": (ctypes.c_int, [_ctxp, ctypes.c_int]),
+    "svt_set_tau": (ctypes.c_int, [_ctxp, ctypes.c_double]),
+    "svt_solve_continuation": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, _vp, ctypes.POINTER(svt_result)]),
     "svt_sddmm_update_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,
                                                 _vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _dp, _vp]),
     "svt_noalloc_last_error": (ctypes.c_char_p, []),

@@ -777,6 +777,124 @@ static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out)
   return SVT_OK;
 }
 
+// D_tau(Y) by a randomized range finder (Sec. 6, the first of the two alternatives the paper names):
+// Y ~ Q Q^T Y with Q an orthonormal basis of Y Omega refined by power steps, and D_tau(Q Q^T Y) from the
+// SVD of the small factor.  Every product is the library's sparse product, every basis goes through
+// the block orthonormalisation, and the small SVD is the projected-SVD kernel:
+//   Omega (n x l, warm columns then SplitMix64 columns) -> orthonormalised (same span(Y Omega); it
+//   also writes the float32 copy the float32 products read);  Q = orth(Y Omega);  power steps
+//   Q = orth(Y orth(Y^T Q));  Z = Y^T Q = P R (orthonormalisation with R written to T);
+//   R = Xl diag(theta) Wr^T (projected SVD)  =>  Q^T Y = Z^T = Wr diag(theta) (P Xl)^T, so
+//   U = Q Wr and V = P Xl are the singular vectors of Q Q^T Y with values theta.
+// The rank policy of Sec. 5.1.1 (s_k = r_{k-1} + 1, s_k += l while theta_{s_k} > tau) repeats the
+// pass with the previous pass's right vectors as warm columns.
+static svt_status shrink_randomized(svt_ctx* c, double tau, int s_init, int* r_out) {
+  NvtxRange nv("svt: shrink D_tau (randomized range finder)");
+  const int m = (int)c->m, n = (int)c->n;
+  const int kmin = (int)std::min(c->m, c->n);
+  const int p = c->opt.rsvd_oversample;
+  const int q = c->opt.rsvd_power;
+  double* Q = c->Ub;                 // m x l
+  double* Om = c->Vb;                // n x l
+  double* P = nullptr;               // n x l (block 1 of Vb, placed once l is known)
+  int s = std::min(s_init, kmin);
+  int passes = 0;
+  c->last_cycles = 0;
+  c->last_spmm = 0;
+  for (;;) {
+    if (s + p > kBMax && s < kmin)
+      return fail(c, SVT_ERR_RANK_LIMIT, "randomized shrink: s_k + oversampling = %d exceeds %d test columns", s + p,
+                  kBMax);
+    const int l = std::min(kBMax, (s + p + 7) / 8 * 8);
+    P = c->Vb + (long long)n * l;
+    const int c0 = std::min(c->warm_cols, l);
+    if (c0 > 0)
+      CU(c, cudaMemcpy2DAsync(Om, l * sizeof(double), c->Vwarm, c->warm_cols * sizeof(double), c0 * sizeof(double), n,
+                              cudaMemcpyDeviceToDevice, c->st));
+    const uint64_t seed = c->opt.rsvd_seed + 1000ull * (uint64_t)(c->k + 1) + (uint64_t)passes;
+    if (c0 < l) TRY(launched(c, launch_random_block(Om, n, l, c0, seed, c->st)));
+    ++passes;
+    auto prod = [&](bool transpose, const double* X, const float* Xf, double* Out) -> svt_status {
+      const int n_out = transpose ? n : m;
+      int l2 = prof_launch_f(c, transpose ? SVT_PROF_SPMM_T : SVT_PROF_SPMM,
+                             spmm_bytes(c, n_out, transpose ? m : n, l), 2.0 * c->nnz * l, [&] {
+        return transpose ? launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), X, Xf, Out, n, l, c->st, c->nnz)
+                         : launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), X, Xf, Out, m, l, c->st, c->nnz);
+      });
+      c->last_spmm += 1;
+      c->total_spmm += 1;
+      return launched(c, l2);
+    };
+    TRY(orthonormalize(c, Om, nullptr, 0, 0, n, l, nullptr, nullptr, c->Vsh));
+    TRY(prod(false, Om, c->Vsh, Q));
+    TRY(orthonormalize(c, Q, nullptr, 0, 0, m, l, nullptr, nullptr, c->Ush));
+    for (int it = 0; it < q; ++it) {
+      TRY(prod(true, Q, c->Ush, P));
+      TRY(orthonormalize(c, P, nullptr, 0, 0, n, l, nullptr, nullptr, c->Vsh));
+      TRY(prod(false, P, c->Vsh, Q));
+      TRY(orthonormalize(c, Q, nullptr, 0, 0, m, l, nullptr, nullptr, c->Ush));
+    }
+    TRY(prod(true, Q, c->Ush, P));
+    CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
+    TRY(orthonormalize(c, P, nullptr, 0, 0, n, l, nullptr, c->T, c->Vsh));
+    const double tol_j = std::max(1e-15, 2.0 * l * 1.1102230246251565e-16);
+    int lj = prof_launch(c, SVT_PROF_JACOBI, 24.0 * l * l, [&] {
+      if (c->prec == SVT_FP64)
+        return launch_small_svd(c->T, kKMax, l, nullptr, l, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
+                                c->dcount, c->st);
+      return launch_small_svd_mixed(c->T, kKMax, l, nullptr, l, c->theta, c->Xl, c->Wr, c->res, l, c->wsrc, 2e-6, 60,
+                                    c->err, c->dcount, c->st);
+    });
+    TRY(launched(c, lj));
+    CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * l, cudaMemcpyDeviceToHost, c->st));
+    c->last_cycles += 1;
+    c->total_cycles += 1;
+    TRY(sync_and_check(c));
+    const double* th = c->h_pin;
+    if (!std::isfinite(th[0])) return fail(c, SVT_ERR_NUMERIC, "non-finite singular value estimate");
+    // right singular vectors of this pass, V = P Xl (all l): the warm columns of the next pass or shrink
+    int lc = prof_launch(c, SVT_PROF_COMBINE, 8.0 * (double)n * 2 * l, [&] {
+      return launch_basis_combine(P, (long long)n * l, 1, l, n, c->Xl, l, l, nullptr, c->Vwarm, c->st);
+    });
+    TRY(launched(c, lc));
+    c->warm_cols = l;
+    const int s_eff = std::min(s, l);
+    if (s_eff < kmin && th[s_eff - 1] > tau) {
+      s = std::min(s + c->opt.ell, kmin);
+      continue;
+    }
+    int r = 0;
+    while (r < l && th[r] > tau) ++r;
+    if (r > c->max_rank) return fail(c, SVT_ERR_RANK_LIMIT, "rank %d exceeds max_rank %d", r, c->max_rank);
+    c->d_host.assign(r, 0.0);
+    for (int i = 0; i < r; ++i) c->d_host[i] = th[i] - tau;
+    c->last_s = s_eff;
+    c->last_passes = passes;
+    c->last_sigma1 = th[0];
+    if (r > 0) {
+      std::memcpy(c->h_pin + 2 * kKMax, c->d_host.data(), sizeof(double) * r);
+      CU(c, cudaMemcpyAsync(c->scale, c->h_pin + 2 * kKMax, sizeof(double) * r, cudaMemcpyHostToDevice, c->st));
+      c->ldf = (r + 3) & ~3;
+      int l3 = prof_launch(c, SVT_PROF_COMBINE, 8.0 * (2.0 * m * (l + r) + n * (l + r)), [&] {
+        return launch_basis_combine(Q, (long long)m * l, 1, l, m, c->Wr, l, r, nullptr, c->Uf, c->st) +
+               launch_basis_combine(Q, (long long)m * l, 1, l, m, c->Wr, l, r, c->scale, c->Ut, c->st, c->Utf,
+                                    c->ldf) +
+               launch_basis_combine(P, (long long)n * l, 1, l, n, c->Xl, l, r, nullptr, c->Vf, c->st, c->Vff,
+                                    c->ldf);
+      });
+      TRY(launched(c, l3));
+    }
+    c->r = r;
+    *r_out = r;
+    return SVT_OK;
+  }
+}
+
+static svt_status shrink_dispatch(svt_ctx* c, double tau, int s_init, int* r_out) {
+  if (c->opt.shrink_engine == SVT_SHRINK_RANDOMIZED) return shrink_randomized(c, tau, s_init, r_out);
+  return shrink_current(c, tau, s_init, r_out);
+}
+
 // ------------------------------------------------------------------------------------------------
 // C-ABI
 // ------------------------------------------------------------------------------------------------
@@ -802,6 +920,10 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->device_alloc = nullptr;
   opt->device_free = nullptr;
   opt->alloc_user = nullptr;
+  opt->shrink_engine = SVT_SHRINK_LANCZOS;
+  opt->rsvd_oversample = 8;
+  opt->rsvd_power = 1;
+  opt->rsvd_seed = 0;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -1063,6 +1185,13 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   if (!(o.orth_repass == o.orth_repass)) return fail(nullptr, SVT_ERR_ARG, "orth_repass is NaN");
   if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
     return fail(nullptr, SVT_ERR_ARG, "device_alloc and device_free must be given together");
+  if (o.shrink_engine != SVT_SHRINK_LANCZOS && o.shrink_engine != SVT_SHRINK_RANDOMIZED)
+    return fail(nullptr, SVT_ERR_ARG, "unknown shrink engine");
+  if (o.shrink_engine == SVT_SHRINK_RANDOMIZED &&
+      (std::min(m, n) < 32 || o.rsvd_oversample < 1 || o.rsvd_oversample > 24 || o.rsvd_power < 0 ||
+       o.rsvd_power > 8))
+    return fail(nullptr, SVT_ERR_ARG,
+                "randomized shrink needs min(m, n) >= 32, 1 <= rsvd_oversample <= 24, 0 <= rsvd_power <= 8");
   if (o.ell < 1) o.ell = 5;
   if (o.k_max < 1) o.k_max = 1000;
   if (o.lanczos_steps < 1) o.lanczos_steps = 3;
@@ -1131,6 +1260,8 @@ extern "C" svt_status svt_configure(svt_ctx* c, double tau, double delta, double
     return fail(c, SVT_ERR_NUMERIC, c->ds_E > 0.0 ? "soft_E(B) is zero: X = 0 already meets |B - X| <= E"
                                                   : "||P_Omega M||_2 is zero");
   TRY(keep_ritz(c, b, J, std::min(b, 8)));
+  // the randomized engine's first shrink starts from random test columns only
+  if (c->opt.shrink_engine == SVT_SHRINK_RANDOMIZED) c->warm_cols = 0;
   if (k0 >= 0) c->k0 = k0;
   else c->k0 = (int64_t)std::ceil(c->tau / (c->delta * c->norm2));
   if (c->ds_E > 0.0)
@@ -1185,7 +1316,7 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
   CU(c, cudaEventRecord(c->ev0, c->st));
   int r = 0;
-  TRY(shrink_current(c, c->tau, c->r + 1, &r));
+  TRY(shrink_dispatch(c, c->tau, c->r + 1, &r));
   const int nxt = 1 - c->ycur;
   NvtxRange nv_upd("svt: fused X on Omega + dual step + residual");
   SddmmDual dual{c->Yp[c->ycur], c->Ym[c->ycur], c->Yp[nxt], c->Ym[nxt], c->ds_E};
@@ -1270,6 +1401,67 @@ extern "C" svt_status svt_solve(svt_ctx* c, double tau, double delta, double eps
   return s;
 }
 
+extern "C" svt_status svt_set_tau(svt_ctx* c, double tau) {
+  if (!c) return SVT_ERR_ARG;
+  if (!(tau > 0.0) || !std::isfinite(tau)) return fail(c, SVT_ERR_ARG, "tau must be positive and finite");
+  if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
+  c->tau = tau;
+  c->k = 0;
+  return SVT_OK;
+}
+
+extern "C" svt_status svt_solve_continuation(svt_ctx* c, const double* taus, int n_tau, double delta, double eps,
+                                             int max_rank, int64_t* stage_iters, svt_result* out) {
+  if (!c) return SVT_ERR_ARG;
+  if (!taus || n_tau < 1) return fail(c, SVT_ERR_ARG, "need n_tau >= 1 values of tau");
+  for (int i = 0; i < n_tau; ++i)
+    if (!(taus[i] > 0.0) || !std::isfinite(taus[i])) return fail(c, SVT_ERR_ARG, "every tau must be positive");
+  NvtxRange nv("svt_solve_continuation");
+  StreamJoin join(c);
+  cudaEvent_t e0, e1;
+  CU(c, cudaEventCreate(&e0));
+  CU(c, cudaEventCreate(&e1));
+  CU(c, cudaEventRecord(e0, c->st));
+  const int64_t spmm0 = c->total_spmm, cyc0 = c->total_cycles;
+  svt_status s = svt_configure(c, taus[0], delta, eps, max_rank, -1);
+  svt_step_info info{};
+  info.residual = INFINITY;
+  bool converged = false;
+  int64_t total = 0;
+  for (int i = 0; i < n_tau && s == SVT_OK; ++i) {
+    if (i > 0) s = svt_set_tau(c, taus[i]);
+    converged = false;
+    int64_t it = 0;
+    while (s == SVT_OK && it < c->opt.k_max) {
+      ++it;
+      s = svt_step(c, &info);
+      if (s == SVT_STOPPED) { converged = true; s = SVT_OK; break; }
+    }
+    if (stage_iters) stage_iters[i] = it;
+    total += it;
+    if (s == SVT_OK && !converged) s = fail(c, SVT_ERR_NOT_CONVERGED, "k_max iterations reached in stage %d", i);
+  }
+  cudaEventRecord(e1, c->st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (out) {
+    out->iterations = total;
+    out->k0 = c->k0;
+    out->rank = c->r;
+    out->converged = converged ? 1 : 0;
+    out->residual = info.residual;
+    out->norm2_M = c->norm2;
+    out->normF_M = c->normF;
+    out->ms = ms;
+    out->spmm_calls = c->total_spmm - spmm0;
+    out->lanczos_cycles = c->total_cycles - cyc0;
+  }
+  return s;
+}
+
 extern "C" svt_status svt_get_rank(const svt_ctx* c, int* r) {
   if (!c || !r) return SVT_ERR_ARG;
   *r = c->r;
@@ -1337,7 +1529,7 @@ extern "C" svt_status svt_shrink(svt_ctx* c, double tau, int* r_out, double* sig
   if (!(tau > 0)) return fail(c, SVT_ERR_ARG, "tau must be positive (or configured)");
   if (c->max_rank < 1) c->max_rank = kMaxRankCap;
   int r = 0;
-  TRY(shrink_current(c, tau, c->r + 1, &r));
+  TRY(shrink_dispatch(c, tau, c->r + 1, &r));
   TRY(sync_and_check(c));
   if (r_out) *r_out = r;
   if (sigma)

@@ -56,12 +56,12 @@ struct Rot<float> {
   // from the hardware reciprocal / reciprocal-square-root approximations (a few ulp): c^2 + s^2 = 1
   // to ~1e-7, the level of the float32 rotations themselves.  For |zeta| >= 2^40, sqrt(1 + zeta^2)
   // is taken as |zeta| (t ~ 1 / (2 zeta)), which also keeps zeta^2 clear of overflow.
-  static __device__ __forceinline__ void params(float al, float be, float ga, float& c, float& s) {
+  static __device__ __forceinline__ void params(float al, float be, float ga, float& c, float& s, float& t) {
     const float zeta = __fdividef(be - al, 2.f * ga);
     const float az = fabsf(zeta);
     const float z2 = fmaf(zeta, zeta, 1.f);
     const float h = az < 1.0995116e12f ? z2 * rsqrtf(z2) : az;
-    const float t = copysignf(__fdividef(1.f, az + h), zeta);
+    t = copysignf(__fdividef(1.f, az + h), zeta);
     c = rsqrtf(fmaf(t, t, 1.f));
     s = c * t;
   }
@@ -73,11 +73,11 @@ struct Rot<float> {
 
 template <>
 struct Rot<double> {
-  static __device__ __forceinline__ void params(double al, double be, double ga, double& c, double& s) {
+  static __device__ __forceinline__ void params(double al, double be, double ga, double& c, double& s, double& t) {
     const double zeta = (be - al) * rcp_nr(2.0 * ga);
     const double z2 = fma(zeta, zeta, 1.0);
     const double h = z2 * rsqrt_nr(z2, 2);                 // sqrt(1 + zeta^2)
-    const double t = copysign(1.0, zeta) * rcp_nr(fabs(zeta) + h);
+    t = copysign(1.0, zeta) * rcp_nr(fabs(zeta) + h);
     c = rsqrt_nr(fma(t, t, 1.0), 2);
     s = c * t;
   }
@@ -98,9 +98,12 @@ static constexpr int JL = 8;
 template <typename R>
 __device__ __forceinline__ R shfl_grp(R v, int o) { return shfl_xor_r(v, o); }
 
-template <typename R, int JR, bool ACC>   // JR = rows per lane = ceil(K / JL), a compile-time bound
+// TRACK: the squared column norms are kept in nrm2 (shared memory, filled by the caller) and
+// updated by every rotation (al' = al - t ga, be' = be + t ga with t = s / c), so a pair needs one
+// inner product instead of three.
+template <typename R, int JR, bool ACC, bool TRACK = false>   // JR = rows per lane = ceil(K / JL)
 __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag,
-                             bool quad_stop = false) {
+                             bool quad_stop = false, R* nrm2 = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int gl = lane & (JL - 1);                 // lane inside the pair group
   const int gsub = lane / JL;                     // pair slot inside the warp
@@ -137,22 +140,34 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
         }
 #pragma unroll
         for (int k = 0; k < JR; ++k) {
-          al += a[k] * a[k];
-          be += bq[k] * bq[k];
+          if (!TRACK) {
+            al += a[k] * a[k];
+            be += bq[k] * bq[k];
+          }
           ga += a[k] * bq[k];
         }
 #pragma unroll
         for (int o = 1; o < JL; o <<= 1) {
-          al += shfl_grp(al, o);
-          be += shfl_grp(be, o);
+          if (!TRACK) {
+            al += shfl_grp(al, o);
+            be += shfl_grp(be, o);
+          }
           ga += shfl_grp(ga, o);
+        }
+        if (TRACK && has) {
+          al = nrm2[p];
+          be = nrm2[q];
         }
         if (has && ga != R(0)) {
           const R cs = Rot<R>::cosang(al, be, ga);
           if (cs > tol) {
             my_max = fmaxf(my_max, (float)cs);
-            R c, s;
-            Rot<R>::params(al, be, ga, c, s);
+            R c, s, t;
+            Rot<R>::params(al, be, ga, c, s, t);
+            if (TRACK && gl == 0) {
+              nrm2[p] = al - t * ga;
+              nrm2[q] = be + t * ga;
+            }
 #pragma unroll
             for (int k = 0; k < JR; ++k) {
               const int r = gl + JL * k;
@@ -221,11 +236,13 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 // float64 path in two phases.  One float64 rotation costs ~20 dependent float64 operations and its
 // column updates run on the float64 pipe (2 FMA per clock per SM on GB300), so full float64 sweeps
 // from T take milliseconds.  Instead:
-//   A. float32 sweeps on the columns of T with the rotations accumulated in W (float32): this
-//      converges the angles to the float32 level (|cos| ~ 1e-6);
+//   A. float32 sweeps on the columns of T with the rotations accumulated in W (float32), until
+//      every pair has |cos| <= 3e-5;
 //   B. in float64: W <- W (I - (W^T W - I) / 2) (one first-order step back to orthonormality,
-//      1e-12), G = T W, and float64 sweeps on (G, W) from there: quadratic convergence takes the
-//      float32-level angles to the float64 tolerance in two sweeps.
+//      ~1e-12), G = T W, and float64 sweeps on G from there (column norms tracked through the
+//      rotations, W not rotated): quadratic convergence takes |cos| from 3e-5 to ~1e-9 in one
+//      sweep and to the float64 tolerance in the next.  The right vectors of the leading b
+//      triplets are then w = T^T g / ||g||^2 for the final columns g = theta x of G.
 // The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
 template <int JR>
 __global__ void __launch_bounds__(512)
@@ -251,7 +268,7 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
   build_schedule(sched, K);
   __syncthreads();
   // A. float32 sweeps (the float32 rounding level of the angles)
-  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
+  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 3e-5f, max_sweeps, &flag);
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) W[e] = (double)W32[e];
   __syncthreads();
   // B1. E = W^T W - I (upper triangle, into G), then W <- W (I - E / 2) row by row (a row of the
@@ -322,8 +339,19 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     G[c * K + i] = s0 + s1;
   }
   __syncthreads();
-  // B3. float64 sweeps from the float32-level angles
-  const int sweeps_b = jacobi_sweeps<double, JR, true>(G, W, sched, K, tol, max_sweeps, &flag, true);
+  // B3. float64 sweeps from the float32-level angles on G alone (tracked column norms); the right
+  // vectors are formed afterwards from T^T
+  {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < K; c += nw) {
+      double s2 = 0.0;
+      for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
+      s2 = warp_sum(s2);
+      if (lane == 0) nrm[c] = s2;
+    }
+  }
+  __syncthreads();
+  const int sweeps_b = jacobi_sweeps<double, JR, false, true>(G, W, sched, K, tol, max_sweeps, &flag, true, nrm);
   const int sweeps = sweeps_a + sweeps_b;
   if (threadIdx.x == 0) {
     if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
@@ -351,9 +379,30 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     const int i = e / K, k = e - i * K;
     const int c = order[k];
     Xl[i * K + k] = G[c * K + i] * rnrm[c];
-    Wr[i * K + k] = W[c * K + i];
   }
   for (int k = threadIdx.x; k < K; k += blockDim.x) theta[k] = nrm[order[k]];
+  // right vectors of the leading b triplets: w_k = T^T x_k / theta_k = T^T g_k / theta_k^2 (column
+  // i of T has no entries below its diagonal block); the others are not used by the solver and are
+  // left zero
+  const int nv = b < K ? b : K;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e / K, k = e - i * K;
+    double v = 0.0;
+    if (k < nv) {
+      const int c = order[k];
+      const double* gc = G + c * K;
+      const int rend = min(K, (i / b + 1) * b);
+      double s0 = 0.0, s1 = 0.0;
+      int r = 0;
+      for (; r + 1 < rend; r += 2) {
+        s0 += T[(long long)r * ldT + i] * gc[r];
+        s1 += T[(long long)(r + 1) * ldT + i] * gc[r + 1];
+      }
+      if (r < rend) s0 += T[(long long)r * ldT + i] * gc[r];
+      v = (s0 + s1) * (rnrm[c] * rnrm[c]);
+    }
+    Wr[i * K + k] = v;
+  }
   // residual estimates, one warp per triplet
   for (int k = warp; k < K; k += nw) {
     double r2 = 0.0;
