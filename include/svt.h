@@ -360,6 +360,16 @@ svt_status svt_load_state(svt_ctx* ctx, const void* buf, size_t bytes);
  */
 svt_status svt_set_barrier_spins(svt_ctx* ctx, int spins);
 
+/*
+ * Self-test of the library's own float64 reciprocal and reciprocal-square-root helpers (Newton's
+ * iteration from the float32 hardware approximations; the paper has no counterpart).  For the n
+ * device values x (normal positive doubles) writes, to the device array out (5 n doubles, row i =
+ * input i): 1/x with two and with one Newton step, 1/sqrt(x) with two and with one step, and the
+ * Cholesky pivot's 1/sqrt(x) (exponent halved exactly, one step).  Synchronises `stream`.
+ * Errors: SVT_ERR_ARG, SVT_ERR_CUDA (message in svt_last_error(NULL)).
+ */
+svt_status svt_selftest_math(int64_t n, const double* x, double* out, void* stream);
+
 /* Device kernels launched by this library so far on ctx (for launch accounting). */
 int64_t svt_kernel_launches(const svt_ctx* ctx);
 

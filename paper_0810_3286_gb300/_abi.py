@@ -204,6 +204,7 @@ PROTOTYPES = {
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
     "svt_set_barrier_spins": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "svt_set_tau": (ctypes.c_int, [_ctxp, ctypes.c_double]),
+    "svt_selftest_math": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp]),
     "svt_solve_continuation": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, _vp, ctypes.POINTER(svt_result)]),
     "svt_sddmm_update_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, _vp, _vp, _vp,

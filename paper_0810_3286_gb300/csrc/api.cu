@@ -515,9 +515,12 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
   // dimension b, so compact it first.
   CU(c, cudaMemcpy2DAsync(c->Rkeep, b * sizeof(double), c->S, kKMax * sizeof(double), b * sizeof(double), b,
                           cudaMemcpyDeviceToDevice, c->st));
-  // one-sided Jacobi stops when every column pair is orthogonal to the rounding level of a length-K
-  // dot product
-  const double tol_j = std::max(1e-15, 2.0 * K * 1.1102230246251565e-16);
+  // one-sided Jacobi stops when every column pair is orthogonal to 1e-11: Ritz vectors and values
+  // three orders beyond the float64 path's Lanczos tolerance (1e-8 sigma_1), and the float64
+  // kernel then finishes in one float64 sweep after its float32 preconditioning
+  const double tol_j = c->opt.lanczos_tol > 0 && c->opt.lanczos_tol < 1e-9
+                           ? std::max(1e-15, 2.0 * K * 1.1102230246251565e-16)
+                           : 1e-11;
   l += prof_launch(c, SVT_PROF_JACOBI, 24.0 * K * K, [&] {
     if (c->prec == SVT_FP64)
       return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
@@ -1757,6 +1760,20 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
                                      c->Ybc[c->ycur], c->nnz, c->st)));
   }
   return sync_and_check(c);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Self-test of the Newton helpers
+// ------------------------------------------------------------------------------------------------
+extern "C" svt_status svt_selftest_math(int64_t n, const double* x, double* out, void* stream) {
+  if (n < 0 || (n > 0 && (!x || !out))) return fail(nullptr, SVT_ERR_ARG, "svt_selftest_math: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_newton_selftest(x, n, out, st);
+  launch_pivot_selftest(x, n, out, st);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, SVT_ERR_CUDA, "svt_selftest_math: %s", cudaGetErrorString(e));
+  return SVT_OK;
 }
 
 // ------------------------------------------------------------------------------------------------

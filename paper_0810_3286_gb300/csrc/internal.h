@@ -107,6 +107,11 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, do
                      double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
                      cudaStream_t st);
 
+// Self-tests of the Newton helpers (out: 5 doubles per input): slots 0..3 rcp (2 steps, 1 step),
+// rsqrt (2 steps, 1 step) of jacobi.cu; slot 4 the pivot rsqrt of orth.cu.
+int launch_newton_selftest(const double* x, long long n, double* out, cudaStream_t st);
+int launch_pivot_selftest(const double* x, long long n, double* out, cudaStream_t st);
+
 // Sets the dynamic shared-memory limits of the projected-SVD kernels (call before any stream
 // capture); returns 0 on success.
 int init_jacobi_attributes();

@@ -35,11 +35,18 @@ static constexpr int JMAXK = 96;
 static constexpr int kJacobiOnRows = 1;
 static constexpr int JMAXB = 32;
 
+// Reciprocal and reciprocal square root in float64 by Newton's iteration from the float32 hardware
+// approximations (GB300's float64 divide and square root take ~650 cycles): each step squares the
+// relative error, 2^-23 -> ~1e-14 -> rounding.
 __device__ __forceinline__ double rcp_nr(double x) {
   double y = (double)__frcp_rn((float)x);
   y = y * (2.0 - x * y);
   y = y * (2.0 - x * y);
   return y;
+}
+__device__ __forceinline__ double rcp_nr1(double x) {
+  const double y = (double)__frcp_rn((float)x);
+  return y * (2.0 - x * y);
 }
 __device__ __forceinline__ double rsqrt_nr(double x, int steps) {
   double y = (double)rsqrtf((float)x);
@@ -73,12 +80,16 @@ struct Rot<float> {
 
 template <>
 struct Rot<double> {
+  // One Newton step on each float32 seed (reciprocal y <- y (2 - x y), reciprocal square root
+  // y <- y (3/2 - x y^2 / 2)): relative errors ~1e-14, so c^2 + s^2 = 1 to ~1e-14 -- ample for the
+  // finishing sweep, whose rotations are within 1e-5 of the identity -- with half the dependent
+  // float64 operations of two steps.
   static __device__ __forceinline__ void params(double al, double be, double ga, double& c, double& s, double& t) {
-    const double zeta = (be - al) * rcp_nr(2.0 * ga);
+    const double zeta = (be - al) * rcp_nr1(2.0 * ga);
     const double z2 = fma(zeta, zeta, 1.0);
-    const double h = z2 * rsqrt_nr(z2, 2);                 // sqrt(1 + zeta^2)
-    t = copysign(1.0, zeta) * rcp_nr(fabs(zeta) + h);
-    c = rsqrt_nr(fma(t, t, 1.0), 2);
+    const double h = z2 * rsqrt_nr(z2, 1);                 // sqrt(1 + zeta^2)
+    t = copysign(1.0, zeta) * rcp_nr1(fabs(zeta) + h);
+    c = rsqrt_nr(fma(t, t, 1.0), 1);
     s = c * t;
   }
   static __device__ __forceinline__ double cosang(double al, double be, double ga) {
@@ -101,12 +112,14 @@ __device__ __forceinline__ R shfl_grp(R v, int o) { return shfl_xor_r(v, o); }
 // TRACK: the squared column norms are kept in nrm2 (shared memory, filled by the caller) and
 // updated by every rotation (al' = al - t ga, be' = be + t ga with t = s / c), so a pair needs one
 // inner product instead of three.
-template <typename R, int JR, bool ACC, bool TRACK = false>   // JR = rows per lane = ceil(K / JL)
+// JLv: lanes per pair (JL by default; fewer lanes put more pairs in one warp instruction, which
+// pays where the instruction count is the bound: the float64 pipe).
+template <typename R, int JR, bool ACC, bool TRACK = false, int JLv = JL>   // JR = rows per lane = ceil(K / JLv)
 __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R tol, int max_sweeps, int* flag,
                              bool quad_stop = false, R* nrm2 = nullptr) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int gl = lane & (JL - 1);                 // lane inside the pair group
-  const int gsub = lane / JL;                     // pair slot inside the warp
+  const int gl = lane & (JLv - 1);                // lane inside the pair group
+  const int gsub = lane / JLv;                    // pair slot inside the warp
   const int npairs = K / 2;
   __shared__ float warp_max[32];   // per-warp largest |cos| between a rotated pair in this sweep
   int sweep = 0;
@@ -117,7 +130,7 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
     __syncthreads();
     for (int round = 0; round < K - 1; ++round) {
       const unsigned char* rs = sched + 2 * round * npairs;
-      for (int base = warp * (32 / JL); base < npairs; base += nw * (32 / JL)) {   // warp-uniform
+      for (int base = warp * (32 / JLv); base < npairs; base += nw * (32 / JLv)) {   // warp-uniform
         const int pr = base + gsub;
         const bool has = pr < npairs;
         const int p = has ? rs[2 * pr] : 0, q = has ? rs[2 * pr + 1] : 0;
@@ -131,7 +144,7 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
         R al = 0, be = 0, ga = 0;
 #pragma unroll
         for (int k = 0; k < JR; ++k) {
-          const int r = gl + JL * k;
+          const int r = gl + JLv * k;
           const bool in = has && r < K;
           a[k] = in ? gp[r] : R(0);
           bq[k] = in ? gq[r] : R(0);
@@ -147,7 +160,7 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
           ga += a[k] * bq[k];
         }
 #pragma unroll
-        for (int o = 1; o < JL; o <<= 1) {
+        for (int o = 1; o < JLv; o <<= 1) {
           if (!TRACK) {
             al += shfl_grp(al, o);
             be += shfl_grp(be, o);
@@ -170,7 +183,7 @@ __device__ int jacobi_sweeps(R* G, R* W, const unsigned char* sched, int K, R to
             }
 #pragma unroll
             for (int k = 0; k < JR; ++k) {
-              const int r = gl + JL * k;
+              const int r = gl + JLv * k;
               if (r < K) {
                 gp[r] = c * a[k] - s * bq[k];
                 gq[r] = s * a[k] + c * bq[k];
@@ -237,12 +250,14 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 // column updates run on the float64 pipe (2 FMA per clock per SM on GB300), so full float64 sweeps
 // from T take milliseconds.  Instead:
 //   A. float32 sweeps on the columns of T with the rotations accumulated in W (float32), until
-//      every pair has |cos| <= 3e-5;
+//      every pair has |cos| <= 2e-6;
 //   B. in float64: W <- W (I - (W^T W - I) / 2) (one first-order step back to orthonormality,
 //      ~1e-12), G = T W, and float64 sweeps on G from there (column norms tracked through the
-//      rotations, W not rotated): quadratic convergence takes |cos| from 3e-5 to ~1e-9 in one
-//      sweep and to the float64 tolerance in the next.  The right vectors of the leading b
-//      triplets are then w = T^T g / ||g||^2 for the final columns g = theta x of G.
+//      rotations, W not rotated, four lanes per pair): quadratic convergence takes |cos| from
+//      2e-6 to ~1e-11 in one sweep, and a sweep whose pairs all had |cos| <= sqrt(tol) is the
+//      last (the caller's tol is 1e-11: Ritz vectors far more accurate than the Lanczos
+//      tolerance of 1e-8 sigma_1 they are tested against).  The right vectors of the leading
+//      b triplets are then w = T^T g / ||g||^2 for the final columns g = theta x of G.
 // The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
 template <int JR>
 __global__ void __launch_bounds__(512)
@@ -268,7 +283,7 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
   build_schedule(sched, K);
   __syncthreads();
   // A. float32 sweeps (the float32 rounding level of the angles)
-  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 3e-5f, max_sweeps, &flag);
+  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) W[e] = (double)W32[e];
   __syncthreads();
   // B1. E = W^T W - I (upper triangle, into G), then W <- W (I - E / 2) row by row (a row of the
@@ -351,7 +366,7 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     }
   }
   __syncthreads();
-  const int sweeps_b = jacobi_sweeps<double, JR, false, true>(G, W, sched, K, tol, max_sweeps, &flag, true, nrm);
+  const int sweeps_b = jacobi_sweeps<double, 2 * JR, false, true, JL / 2>(G, W, sched, K, tol, max_sweeps, &flag, true, nrm);
   const int sweeps = sweeps_a + sweeps_b;
   if (threadIdx.x == 0) {
     if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
@@ -551,6 +566,26 @@ k_ritz_refine(const double* __restrict__ T, int ldT, int K, const double* __rest
     r2 = warp_sum(r2);
   }
   if (lane == 0) res[k] = sqrt(r2);
+}
+
+// Self-test of the Newton reciprocal / reciprocal-square-root helpers: out[5 i + 0..3] =
+// rcp_nr(x_i), rcp_nr1(x_i), rsqrt_nr(x_i, 2), rsqrt_nr(x_i, 1) (slot 4 is the orthonormalisation's
+// pivot helper, filled by launch_pivot_selftest).
+__global__ void k_newton_selftest(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[5 * i + 0] = rcp_nr(v);
+    out[5 * i + 1] = rcp_nr1(v);
+    out[5 * i + 2] = rsqrt_nr(v, 2);
+    out[5 * i + 3] = rsqrt_nr(v, 1);
+  }
+}
+
+int launch_newton_selftest(const double* x, long long n, double* out, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int blocks = (int)svt_min_ll(svt_ceil_div(n, 256), 152LL * 4);
+  k_newton_selftest<<<blocks, 256, 0, st>>>(x, n, out);
+  return 1;
 }
 
 static int jacobi_threads(int K) {

@@ -305,7 +305,9 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
 // Columns that lost all but 1e-12 of their norm (or whose pivot is not a normal positive double
 // above 2^-1021) are deflated: R's row is zero and 1 / R_jj = 0.
 // ------------------------------------------------------------------------------------------------
-// Reciprocal square root of a normal positive double (biased exponent 2 .. 2046) to ~1e-13.
+// Reciprocal square root of a normal positive double (biased exponent 2 .. 2046) to ~1e-13: the
+// seed halves the exponent exactly and takes a float32 rsqrt of the mantissa, then one step of
+// Newton's iteration for 1/sqrt(d), y <- y + y (1 - d y^2) / 2, squares its relative error.
 __device__ __forceinline__ double rsqrt_pivot(double d) {
   const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
   const int E = (int)((hi >> 20) & 0x7FFu);
@@ -320,6 +322,19 @@ __device__ __forceinline__ double rsqrt_pivot(double d) {
   const double t = h * y0;
   const double u = fma(-t, y0, 0.5);              // (1 - d y0^2) / 2
   return fma(y0, u, y0);
+}
+
+// Self-test of rsqrt_pivot: out[5 i + 4] = rsqrt_pivot(x_i) (x_i a normal positive double).
+__global__ void k_pivot_selftest(const double* __restrict__ x, long long n, double* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[5 * i + 4] = rsqrt_pivot(x[i]);
+}
+
+int launch_pivot_selftest(const double* x, long long n, double* out, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const int blocks = (int)svt_min_ll(svt_ceil_div(n, 256), 152LL * 4);
+  k_pivot_selftest<<<blocks, 256, 0, st>>>(x, n, out);
+  return 1;
 }
 
 // One warp (lanes 0..31 of the calling warp).  G1 / G2 may have been written by other CTAs of the

@@ -95,3 +95,29 @@ def test_sddmm_update_full_size_sampled(cuda):
     r2 = float(np.sum((p.vals - x_all) ** 2))
     assert abs(res2 - r2) <= 1e-5 * r2
     s.close()
+
+
+def test_newton_helpers_against_cuda_division_and_rsqrt(cuda):
+    """The library's float64 reciprocal / reciprocal square root (Newton's iteration from float32
+    seeds; the Cholesky pivot's variant halves the exponent exactly first, so it covers every normal
+    double) against CUDA's correctly rounded float64 division and square root.  The float32-seeded
+    helpers serve values inside the float32 range (2^-100 .. 2^100 here); the pivot helper is tested
+    over 2^-1000 .. 2^1000.  Relative errors: the square of the seed error (2^-23 for the
+    reciprocal, ~2^-22 for rsqrtf) per single step, plus a few roundings."""
+    torch = cuda
+    from paper_0810_3286_gb300 import library
+    L = library()
+    g = torch.Generator().manual_seed(7)
+    rel = lambda a, b: float(((a - b) / b).abs().max())
+    for lo, hi, slots in ((-100, 100, (0, 1, 2, 3, 4)), (-1000, 1000, (4,))):
+        e = torch.randint(lo, hi, (20000,), generator=g).double()
+        m = 1.0 + torch.rand(20000, generator=g, dtype=torch.float64)
+        x = (m * torch.pow(2.0, e)).cuda()
+        out = torch.empty((20000, 5), dtype=torch.float64, device="cuda")
+        assert L.svt_selftest_math(x.numel(), x.data_ptr(), out.data_ptr(), None) == 0
+        rcp = 1.0 / x
+        rs = 1.0 / torch.sqrt(x)
+        bounds = {0: (rcp, 1e-15), 1: (rcp, 1e-14), 2: (rs, 1e-15), 3: (rs, 2e-13), 4: (rs, 2e-13)}
+        for sl in slots:
+            ref, b = bounds[sl]
+            assert rel(out[:, sl], ref) <= b, (lo, hi, sl, rel(out[:, sl], ref))
