@@ -81,7 +81,8 @@ typedef struct svt_options {
                              at most 32); 0 = automatic: wanted triplets + max(4, wanted / 4) */
   int ell;                /* rank increment l of Sec. 5.1.1 (default 5) */
   int k_max;              /* maximum SVT iterations after the kick (default 1000) */
-  int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J*b <= 96) */
+  int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J b <= 128; raised where a thick restart
+                             keeps several blocks of Ritz pairs, beyond 28 wanted triplets) */
   int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
   double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-8 FP64: per-iterate agreement
                              with a float64 SVT to ~1e-8; 1e-5 FP32 and BF16: ten times the rounding of the
@@ -193,7 +194,7 @@ const char* svt_last_error(const svt_ctx* ctx);
  *   tau       threshold; <= 0 selects 5 sqrt(m n) (Sec. 5.2.1: tau = 5n for square matrices)
  *   delta     step size; <= 0 selects 1.2 m n / nnz (eq. (5.1))
  *   eps       tolerance of the stopping rule eq. (5.5); <= 0 selects 1e-4
- *   max_rank  capacity for the rank of X^k (1 .. 27); exceeding it returns SVT_ERR_RANK_LIMIT
+ *   max_rank  capacity for the rank of X^k (1 .. 64); exceeding it returns SVT_ERR_RANK_LIMIT
  *   k0        >= 0 uses this kick count instead of eq. (5.3); -1 = eq. (5.3)
  * Errors: SVT_ERR_ARG, SVT_ERR_NUMERIC, SVT_ERR_CUDA.
  */

@@ -22,8 +22,9 @@ using namespace svt;
 namespace {
 
 constexpr int kBMax = 32;       // largest Lanczos block
-constexpr int kKMax = 96;       // largest projected problem (J b)
-constexpr int kMaxRankCap = 27; // s_k = r + 1 must leave >= 4 spare columns in a 32-wide block
+constexpr int kKMax = 128;      // largest projected problem (J b)
+constexpr int kGramW = 160;     // widest Gram [Q_0 .. Q_{nq-1}, P] of the orthonormalisation: (nq + 1) b
+constexpr int kMaxRankCap = 64; // rank capacity of X^k
 constexpr int kOversample = 4;  // block columns beyond the wanted triplets
 constexpr uint64_t kStateMagic = 0x5356545354415445ULL;  // "SVTSTATE"
 
@@ -47,7 +48,7 @@ struct svt_ctx {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   struct ProfNode { int cls; double bytes, flops; cudaEvent_t a, b; };
   struct CycleGraph {
-    int b, J, ycur, twoc, thick, Jprev, bf16;
+    int b, J, ycur, twoc, thick, Jprev, bf16, nk;
     unsigned int prof_mask;
     cudaGraphExec_t exec;
     int64_t launches;
@@ -91,8 +92,8 @@ struct svt_ctx {
   double* Ut = nullptr;             // m x kMaxRankCap+1: U diag(sigma - tau)
   double* Uf = nullptr;             // m x cap: U (unscaled)
   double* Vf = nullptr;             // n x cap: V
-  double* Vwarm = nullptr;          // n x kBMax warm start block
-  double* Uwarm = nullptr;          // m x kBMax: left Ritz vectors kept by a thick restart
+  double* Vwarm = nullptr;          // n x kKMax: warm start block; right Ritz vectors kept by a thick restart
+  double* Uwarm = nullptr;          // m x kKMax: left Ritz vectors kept by a thick restart
   // float32 path only: float32 copies of the dense operands of the per-entry kernels (the sparse
   // products read the current basis block, the fused update the factors), written by the kernels
   // that produce the float64 originals
@@ -107,7 +108,7 @@ struct svt_ctx {
   // Lanczos workspace
   double *Ub = nullptr, *Vb = nullptr;   // block bases (blocks of rows x b)
   double *T = nullptr, *S = nullptr, *theta = nullptr, *Xl = nullptr, *Wr = nullptr, *res = nullptr;
-  float* wsrc = nullptr;   // float32 leading Ritz vectors of the projected SVD (kBMax x kKMax)
+  float* wsrc = nullptr;   // float32 leading Ritz vectors of the projected SVD (kKMax x kKMax)
   double *G1 = nullptr, *G2 = nullptr, *G3 = nullptr, *gpart = nullptr, *R1 = nullptr, *dinv = nullptr;
   double *Rkeep = nullptr, *scale = nullptr;
   bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
@@ -354,7 +355,8 @@ static svt_status d2h_sync(svt_ctx* c, void* dst, const void* src, size_t bytes)
 }
 
 // Block size for s_need wanted triplets: s_need plus max(4, s_need / 4) spare columns, at least the
-// block option, rounded up to a multiple of 8, at most kBMax.
+// block option, rounded up to a multiple of 8, at most kBMax.  Beyond 28 wanted triplets the block
+// stays at 32 and a thick restart keeps several blocks of Ritz pairs (cycle_shape).
 static int choose_block(const svt_ctx* c, int s_need) {
   int b = s_need + std::max(kOversample, s_need / 4);
   if (c->opt.block > b) b = c->opt.block;
@@ -362,6 +364,22 @@ static int choose_block(const svt_ctx* c, int s_need) {
   if (b > kBMax) b = kBMax;
   if (b < 8) b = 8;
   return b;
+}
+
+// Shape of the Lanczos cycles for s wanted triplets: block b, block steps J, and nk, the blocks of
+// leading Ritz pairs a thick restart keeps: enough to hold the s wanted ones plus kOversample guard
+// columns (one block up to 28 wanted triplets), with at least one new block per cycle (two where K
+// allows: J = max(lanczos_steps, nk + 2), K = J b <= kKMax).
+static void cycle_shape(const svt_ctx* c, int s, int* b_out, int* J_out, int* nk_out) {
+  const int b = choose_block(c, s);
+  const int Jcap = kKMax / b;
+  int nk = (s + kOversample + b - 1) / b;
+  nk = std::max(1, std::min(nk, Jcap - 1));
+  int J = std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, Jcap);
+  J = std::max(J, std::min(nk + 2, Jcap));
+  *b_out = b;
+  *J_out = std::max(1, J);
+  *nk_out = nk;
 }
 
 static uint64_t next_seed(svt_ctx* c) {
@@ -466,7 +484,7 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
 // an explicit restart from V_0 would build (its next block lies in the span of V_J), for two
 // sparse products and three orthonormalisations less.  Jprev: block steps of the previous cycle
 // (its basis, projected vectors and residual block V_Jprev); the cycle itself may use another J.
-static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
+static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk) {
   const int m = (int)c->m, n = (int)c->n;
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
@@ -475,20 +493,25 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
     CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
     TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
   } else {
+    // the nk b leading Ritz pairs become blocks 0 .. nk-1, block by block (Uwarm / Vwarm hold them
+    // in the block layout of Ub / Vb), and the residual block V_Jprev becomes block nk
     const int Kp = Jprev * b;
-    int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * ((double)m + n) * (Kp + b), [&] {
-      return launch_basis_combine(c->Ub, su, Jprev, b, m, c->Xl, Kp, b, nullptr, c->Uwarm, c->st) +
-             launch_basis_combine(c->Vb, sv, Jprev, b, n, c->Wr, Kp, b, nullptr, c->Vwarm, c->st);
+    int l = prof_launch(c, SVT_PROF_COMBINE, 8.0 * ((double)m + n) * (Kp + nk * b), [&] {
+      int q = 0;
+      for (int j = 0; j < nk; ++j)
+        q += launch_basis_combine(c->Ub, su, Jprev, b, m, c->Xl + j * b, Kp, b, nullptr, c->Uwarm + j * su, c->st) +
+             launch_basis_combine(c->Vb, sv, Jprev, b, n, c->Wr + j * b, Kp, b, nullptr, c->Vwarm + j * sv, c->st);
+      return q;
     });
     TRY(launched(c, l));
-    // V_Jprev -> block 1 (its float32 copy, written by its orthonormalisation, is still in Vsh);
-    // the Ritz vectors -> block 0
-    CU(c, cudaMemcpyAsync(c->Vb + sv, c->Vb + Jprev * sv, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
-    CU(c, cudaMemcpyAsync(c->Vb, c->Vwarm, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
-    CU(c, cudaMemcpyAsync(c->Ub, c->Uwarm, sizeof(double) * su, cudaMemcpyDeviceToDevice, c->st));
+    // V_Jprev -> block nk (its float32 copy, written by its orthonormalisation, is still in Vsh);
+    // the Ritz vectors -> blocks 0 .. nk-1
+    CU(c, cudaMemcpyAsync(c->Vb + nk * sv, c->Vb + Jprev * sv, sizeof(double) * sv, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c->Vb, c->Vwarm, sizeof(double) * nk * sv, cudaMemcpyDeviceToDevice, c->st));
+    CU(c, cudaMemcpyAsync(c->Ub, c->Uwarm, sizeof(double) * nk * su, cudaMemcpyDeviceToDevice, c->st));
     CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
-    TRY(launched(c, launch_set_diagonal(c->T, kKMax, c->theta, b, c->st)));
-    j0 = 1;
+    TRY(launched(c, launch_set_diagonal(c->T, kKMax, c->theta, nk * b, c->st)));
+    j0 = nk;
   }
   int l = 0;
   for (int j = j0; j < J; ++j) {
@@ -521,12 +544,15 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
   const double tol_j = c->opt.lanczos_tol > 0 && c->opt.lanczos_tol < 1e-9
                            ? std::max(1e-15, 2.0 * K * 1.1102230246251565e-16)
                            : 1e-11;
+  // Ritz vectors formed in float64: the nk b that a thick restart of this shape keeps (they cover
+  // every wanted triplet)
+  const int nvec = std::max(1, nk) * b;
   l += prof_launch(c, SVT_PROF_JACOBI, 24.0 * K * K, [&] {
     if (c->prec == SVT_FP64)
-      return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
+      return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, nvec, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
                               c->dcount, c->st);
-    return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, b, c->wsrc, 2e-6, 60,
-                                  c->err, c->dcount, c->st);
+    return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, nvec, c->wsrc, 2e-6,
+                                  60, c->err, c->dcount, c->st);
   });
   TRY(launched(c, l));
   CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
@@ -537,14 +563,14 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev) {
 
 // Captures issue_cycle for this (b, J, Y buffer, correction mode, restart kind) once and replays it
 // afterwards: one graph launch instead of tens of kernel launches per cycle.
-static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jprev) {
+static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk) {
   const int twoc = c->two_corrections ? 1 : 0;
   const int tk = thick ? 1 : 0;
   const int jp = thick ? Jprev : 0;
   const int bf = c->bf16_active ? 1 : 0;
   for (auto& g : c->graphs)
     if (g.b == b && g.J == J && g.ycur == c->ycur && g.twoc == twoc && g.thick == tk && g.Jprev == jp &&
-        g.bf16 == bf && g.prof_mask == c->prof_mask) {
+        g.bf16 == bf && g.nk == nk && g.prof_mask == c->prof_mask) {
       CU(c, cudaGraphLaunch(g.exec, c->st));
       c->launches += g.launches;
       // the graph's event-record nodes fire again on every replay: harvest them at the next sync
@@ -554,7 +580,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
   const int64_t l0 = c->launches;
   const size_t p0 = c->prof_pending.size();
   CU(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-  svt_status s = issue_cycle(c, b, J, thick, Jprev);
+  svt_status s = issue_cycle(c, b, J, thick, Jprev, nk);
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->st, &graph);
   const int64_t nl = c->launches - l0;
@@ -583,7 +609,7 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
     (void)cudaGetLastError();
     return fail(c, SVT_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(e));
   }
-  c->graphs.push_back({b, J, c->ycur, twoc, tk, jp, bf, c->prof_mask, exec, nl, prof});
+  c->graphs.push_back({b, J, c->ycur, twoc, tk, jp, bf, nk, c->prof_mask, exec, nl, prof});
   CU(c, cudaGraphLaunch(exec, c->st));
   c->launches += nl;
   for (auto& pn : prof) c->prof_pending.push_back({pn.cls, pn.bytes, pn.flops, pn.a, pn.b, true});
@@ -591,15 +617,15 @@ static svt_status run_cycle_graph(svt_ctx* c, int b, int J, bool thick, int Jpre
 }
 
 // One cycle, then the host reads the Ritz values and residual estimates (theta/res, pinned).
-static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, const double** theta_h,
+static svt_status lanczos_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk, const double** theta_h,
                                 const double** res_h) {
   NvtxRange nv("svt: Lanczos cycle (SpMM, reorthogonalisation, projected SVD)");
   if (c->opt.use_graphs) {
-    TRY(run_cycle_graph(c, b, J, thick, Jprev));
+    TRY(run_cycle_graph(c, b, J, thick, Jprev, nk));
   } else {
-    TRY(issue_cycle(c, b, J, thick, Jprev));
+    TRY(issue_cycle(c, b, J, thick, Jprev, nk));
   }
-  const int nspmm = 2 * (thick ? J - 1 : J);
+  const int nspmm = 2 * (thick ? J - nk : J);
   c->last_spmm += nspmm;
   c->total_spmm += nspmm;
   c->last_cycles += 1;
@@ -657,8 +683,8 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-8 : 1e-5);
   int s = std::min(s_init, kmin);
   int passes = 1;
-  int b = choose_block(c, s);
-  int J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
+  int b = 0, J = 0, nk = 1;
+  cycle_shape(c, s, &b, &J, &nk);
   c->last_cycles = 0;
   c->last_spmm = 0;
   int warm = std::min(c->warm_cols, b);
@@ -672,7 +698,7 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
   int cyc = 0;
   for (;; ++cyc) {
     const double *th, *rs;
-    TRY(lanczos_cycle(c, b, J, thick, Jprev, &th, &rs));
+    TRY(lanczos_cycle(c, b, J, thick, Jprev, nk, &th, &rs));
     if (!std::isfinite(th[0]) || !std::isfinite(rs[0]))
       return fail(c, SVT_ERR_NUMERIC, "non-finite Ritz value or residual estimate");
     // stagnation: a cluster of Ritz values that the working precision cannot separate further
@@ -709,10 +735,10 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
         }
         s = std::min(s + c->opt.ell, kmin);
         ++passes;
-        int nb = choose_block(c, s);
-        TRY(keep_ritz(c, b, J, std::min(b, nb)));
+        int nb = 0;
+        cycle_shape(c, s, &nb, &J, &nk);
+        TRY(keep_ritz(c, b, Jprev, std::min(b, nb)));
         b = nb;
-        J = std::max(1, std::min(c->opt.lanczos_steps > 0 ? c->opt.lanczos_steps : 3, kKMax / b));
         TRY(set_start_block(c, b, std::min(c->warm_cols, b)));
         cyc = -1;
         continue;
@@ -728,10 +754,11 @@ static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<do
     if (cyc + 1 >= max_cycles)
       return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
                   max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
-    // not converged, same block: continue from the leading Ritz pairs and the residual block,
-    // extending the space by restart_steps - 1 blocks
-    const int Jr = std::max(1, std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : J, kKMax / b));
-    if (Jr >= 2) {
+    // not converged, same block: continue from the leading Ritz pairs (nk blocks) and the residual
+    // block, extending the space by restart_steps - nk blocks
+    int Jr = std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : J, kKMax / b);
+    Jr = std::max(Jr, std::min(nk + 1, kKMax / b));
+    if (Jr >= nk + 1) {
       thick = true;
       J = Jr;
     } else {
@@ -843,7 +870,7 @@ static svt_status shrink_randomized(svt_ctx* c, double tau, int s_init, int* r_o
     const double tol_j = std::max(1e-15, 2.0 * l * 1.1102230246251565e-16);
     int lj = prof_launch(c, SVT_PROF_JACOBI, 24.0 * l * l, [&] {
       if (c->prec == SVT_FP64)
-        return launch_small_svd(c->T, kKMax, l, nullptr, l, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
+        return launch_small_svd(c->T, kKMax, l, nullptr, l, l, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
                                 c->dcount, c->st);
       return launch_small_svd_mixed(c->T, kKMax, l, nullptr, l, c->theta, c->Xl, c->Wr, c->res, l, c->wsrc, 2e-6, 60,
                                     c->err, c->dcount, c->st);
@@ -1077,8 +1104,8 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Ut, (size_t)m * cap));
   TRY(dalloc_t(c, &c->Uf, (size_t)m * cap));
   TRY(dalloc_t(c, &c->Vf, (size_t)n * cap));
-  TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kBMax));
-  TRY(dalloc_t(c, &c->Uwarm, (size_t)m * kBMax));
+  TRY(dalloc_t(c, &c->Vwarm, (size_t)n * kKMax));
+  TRY(dalloc_t(c, &c->Uwarm, (size_t)m * kKMax));
   if (c->bf16_mode) {
     for (int i = 0; i < 2; ++i) {
       TRY(dalloc(c, &c->Yb[i], nnz * 2));
@@ -1100,10 +1127,10 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc_t(c, &c->Xl, (size_t)kKMax * kKMax));
   TRY(dalloc_t(c, &c->Wr, (size_t)kKMax * kKMax));
   TRY(dalloc_t(c, &c->res, kKMax));
-  TRY(dalloc_t(c, &c->wsrc, (size_t)kBMax * kKMax));
-  TRY(dalloc_t(c, &c->G1, 128 * 32));
-  TRY(dalloc_t(c, &c->G2, 128 * 32));
-  TRY(dalloc_t(c, &c->G3, 128 * 32));
+  TRY(dalloc_t(c, &c->wsrc, (size_t)kKMax * kKMax));
+  TRY(dalloc_t(c, &c->G1, kGramW * kBMax));
+  TRY(dalloc_t(c, &c->G2, kGramW * kBMax));
+  TRY(dalloc_t(c, &c->G3, kGramW * kBMax));
   TRY(dalloc_t(c, &c->R1, kBMax * kBMax));
   TRY(dalloc_t(c, &c->R2, kBMax * kBMax));
   TRY(dalloc_t(c, &c->dinv, kBMax));
@@ -1111,8 +1138,8 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   TRY(dalloc(c, &c->gbar, 8));
   CU(c, cudaMemsetAsync(c->gbar, 0, 8, c->st));
   CU(c, cudaMemsetAsync(c->dcount, 0, 8 * sizeof(unsigned long long), c->st));
-  // (nq + 1) b <= 128 columns against b <= 32: at most 128 x 32 entries per row chunk
-  TRY(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax)));
+  // (nq + 1) b <= kGramW columns against b <= 32: at most kGramW x 32 entries per row chunk
+  TRY(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), kGramW / kBMax - 1, kBMax)));
   TRY(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
   TRY(dalloc_t(c, &c->scale, 64));
   TRY(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
@@ -1155,13 +1182,13 @@ extern "C" size_t svt_estimate_device_bytes(int64_t m, int64_t n, int64_t nnz, c
   size_t b = 0;
   b += 4 * (M + 1) + 4 * (N + 1) + 4 * 4 * Z;                 // row_ptr, col_ptr, col_idx, row_idx, perms
   b += 5 * Z * vb;                                           // M, two Y copies in both orders
-  b += 8 * (2 * M + N) * cap + 8 * (M + N) * kBMax;          // factors, warm-start blocks
+  b += 8 * (2 * M + N) * cap + 8 * (M + N) * kKMax;          // factors, warm-start / kept Ritz blocks
   if (bf16) b += 4 * 2 * Z;                                  // bfloat16 copies of Y
   if (o.precision != SVT_FP64) b += 4 * (M + N) * kBMax + 4 * (M + N) * ((cap + 3) & ~3);
   b += 8 * (M + N) * (kKMax + kBMax);                        // Lanczos bases
-  b += 8 * (3 * kKMax * kKMax + kKMax * kBMax + 3 * 128 * 32 + 3 * kBMax * kBMax + 256 + 4096);
-  b += 4 * kBMax * kKMax;                                    // float32 Ritz vectors of the projected SVD
-  b += 8 * (size_t)gram_partial_doubles((int)std::max(m, n), 128 / kBMax - 1, kBMax);
+  b += 8 * (3 * kKMax * kKMax + kKMax * kBMax + 3 * kGramW * kBMax + 3 * kBMax * kBMax + 256 + 4096);
+  b += 4 * kKMax * kKMax;                                    // float32 Ritz vectors of the projected SVD
+  b += 8 * (size_t)gram_partial_doubles((int)std::max(m, n), kGramW / kBMax - 1, kBMax);
   // scratch of the structure build, peak (host inputs staged as int32, int32, float64)
   const size_t nmax = std::max(M, N) + 1;
   size_t pow2 = 1;

@@ -4,6 +4,8 @@
 // (the block orthonormalisation and its Gram products are in orth.cu, the projected SVD in
 // jacobi.cu).  All float64: GB300 executes float64 at ~1/64 of the float32 rate, so these kernels
 // spread the tall products over all SMs.
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -45,6 +47,11 @@ k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b,
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
                          const double* scale, double* Out, cudaStream_t st, float* OutF, int ldF) {
   if (s <= 0 || n <= 0) return 0;
+  // W tiles up to 128 x 64 (64 KB) above the default 48 KB of dynamic shared memory
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_basis_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 64 * (int)sizeof(double));
+  });
   const int rows_per_block = CMB_T / s;
   int blocks = (int)svt_min_ll(svt_ceil_div(n, rows_per_block), 152LL * 8);
   size_t smem = (size_t)nb * b * s * sizeof(double);

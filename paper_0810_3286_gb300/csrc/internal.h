@@ -99,13 +99,14 @@ int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int
                      unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
                      cudaStream_t st, double repass, unsigned int spin_limit);
 
-// Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT): T = Xl diag(theta) Wr^T,
-// theta decreasing; Xl, Wr written K x K row-major.  Also res[i] = || S (Xl rows [K-b, K), column i) ||
+// Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT, block upper triangular with
+// b x b blocks, K <= 128): T = Xl diag(theta) Wr^T, theta decreasing; Xl, Wr written K x K
+// row-major (only the first nv columns of Wr are formed, the others are zero).  Also res[i] = || S (Xl rows [K-b, K), column i) ||
 // for the b x b block S (upper triangular, may be NULL -> res = 0).
 // counters[0] += 1, counters[1] += sweeps.
-int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl, double* Wr,
-                     double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
-                     cudaStream_t st);
+int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta, double* Xl,
+                     double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
+                     unsigned long long* counters, cudaStream_t st);
 
 // Self-tests of the Newton helpers (out: 5 doubles per input): slots 0..3 rcp (2 steps, 1 step),
 // rsqrt (2 steps, 1 step) of jacobi.cu; slot 4 the pivot rsqrt of orth.cu.

@@ -28,12 +28,11 @@
 
 namespace svt {
 
-static constexpr int JMAXK = 96;
+static constexpr int JMAXK = 128;
 // 1: the float32-rotation variant rotates the rows of T (one-sided Jacobi on T^T).  T is upper
 // triangular (block bidiagonal with triangular diagonal blocks, leading diagonal graded by the
 // warm start), and on its rows the sweeps converge in ~10% fewer sweeps than on its columns.
 static constexpr int kJacobiOnRows = 1;
-static constexpr int JMAXB = 32;
 
 // Reciprocal and reciprocal square root in float64 by Newton's iteration from the float32 hardware
 // approximations (GB300's float64 divide and square root take ~650 cycles): each step squares the
@@ -261,13 +260,14 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 // The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
 template <int JR>
 __global__ void __launch_bounds__(512)
-k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b,
+k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b, int nv,
              double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
              double tol, int max_sweeps, unsigned int* err, unsigned long long* counters) {
   extern __shared__ double sm64[];
-  double* W = sm64;                   // K x K column-major: the accumulated rotations (float64, phase B)
-  double* G = W + K * K;              // K x K column-major: T W (phase B); phase A keeps its float32
-                                      // G32 and W32 here
+  // One K x K region: phase A keeps its float32 G32 and W32 there, phase B the float64 W, then
+  // G = T W in its place (column by column); E = W^T W - I is kept in Xl (global) until Xl is
+  // written at the end.
+  double* G = sm64;                   // K x K column-major
   double* nrm = G + K * K;            // K
   double* rnrm = nrm + K;             // K: 1 / nrm (0 for a zero column)
   int* order = (int*)(rnrm + K);      // K
@@ -284,10 +284,19 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
   __syncthreads();
   // A. float32 sweeps (the float32 rounding level of the angles)
   const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) W[e] = (double)W32[e];
-  __syncthreads();
-  // B1. E = W^T W - I (upper triangle, into G), then W <- W (I - E / 2) row by row (a row of the
+  // W (float64) <- W32, in place: W[e] overwrites W32 entries of smaller index only, so chunks of
+  // one entry per thread are read, then written
+  double* W = G;
+  for (int e0 = 0; e0 < K * K; e0 += blockDim.x) {
+    const int e = e0 + threadIdx.x;
+    const float v = e < K * K ? W32[e] : 0.f;
+    __syncthreads();
+    if (e < K * K) W[e] = (double)v;
+    __syncthreads();
+  }
+  // B1. E = W^T W - I (into Xl, global, symmetric), then W <- W (I - E / 2) row by row (a row of the
   // new W needs only the same row of the old one)
+  double* E = Xl;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int p = e / K, q = e - p * K;
     if (q < p) continue;
@@ -301,72 +310,85 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     }
     if (i < K) s0 += wp[i] * wq[i];
     const double v = (s0 + s1) - (p == q ? 1.0 : 0.0);
-    G[q * K + p] = v;
-    G[p * K + q] = v;
+    E[q * K + p] = v;
+    E[p * K + q] = v;
   }
   __syncthreads();
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < K; i += nw) {
-      double wi[(JMAXK + 31) / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  constexpr int NT = (JMAXK + 31) / 32;
+  for (int i = warp; i < K; i += nw) {
+    double wi[NT];
 #pragma unroll
-      for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
-        const int c = lane + 32 * t;
-        wi[t] = c < K ? W[c * K + i] : 0.0;
-      }
-      double out[(JMAXK + 31) / 32];
+    for (int t = 0; t < NT; ++t) {
+      const int c = lane + 32 * t;
+      wi[t] = c < K ? W[c * K + i] : 0.0;
+    }
+    double out[NT];
 #pragma unroll
-      for (int t = 0; t < (JMAXK + 31) / 32; ++t) out[t] = wi[t];
+    for (int t = 0; t < NT; ++t) out[t] = wi[t];
 #pragma unroll
-      for (int tk = 0; tk < (JMAXK + 31) / 32; ++tk) {
-        for (int kk = 0; kk < 32; ++kk) {
-          const int k = 32 * tk + kk;
-          const double wk = __shfl_sync(0xffffffffu, wi[tk], kk);   // W[i, k], held by lane kk
-          if (k >= K) break;                                         // warp-uniform
+    for (int tk = 0; tk < NT; ++tk) {
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = 32 * tk + kk;
+        const double wk = __shfl_sync(0xffffffffu, wi[tk], kk);   // W[i, k], held by lane kk
+        if (k >= K) break;                                         // warp-uniform
 #pragma unroll
-          for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
-            const int c = lane + 32 * t;
-            if (c < K) out[t] = fma(-0.5 * wk, G[c * K + k], out[t]);
-          }
+        for (int t = 0; t < NT; ++t) {
+          const int c = lane + 32 * t;
+          if (c < K) out[t] = fma(-0.5 * wk, __ldcg(E + k * K + c), out[t]);
         }
       }
-      __syncwarp();
+    }
+    __syncwarp();
 #pragma unroll
-      for (int t = 0; t < (JMAXK + 31) / 32; ++t) {
-        const int c = lane + 32 * t;
-        if (c < K) W[c * K + i] = out[t];
-      }
+    for (int t = 0; t < NT; ++t) {
+      const int c = lane + 32 * t;
+      if (c < K) W[c * K + i] = out[t];
     }
   }
   __syncthreads();
-  // B2. G = T W (T block upper triangular: row i has no entries left of its diagonal block)
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int c = e / K, i = e - c * K;
-    const double* trow = T + (long long)i * ldT;
+  // B2. G = T W, one column per warp in place (T block upper triangular: row i has no entries left
+  // of its diagonal block)
+  for (int c = warp; c < K; c += nw) {
     const double* wc = W + c * K;
-    double s0 = 0.0, s1 = 0.0;
-    int k = (i / b) * b;
-    for (; k + 1 < K; k += 2) {
-      s0 += trow[k] * wc[k];
-      s1 += trow[k + 1] * wc[k + 1];
+    double g[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      double s0 = 0.0, s1 = 0.0;
+      if (i < K) {
+        const double* trow = T + (long long)i * ldT;
+        int k = (i / b) * b;
+        for (; k + 1 < K; k += 2) {
+          s0 += trow[k] * wc[k];
+          s1 += trow[k + 1] * wc[k + 1];
+        }
+        if (k < K) s0 += trow[k] * wc[k];
+      }
+      g[t] = s0 + s1;
     }
-    if (k < K) s0 += trow[k] * wc[k];
-    G[c * K + i] = s0 + s1;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int i = lane + 32 * t;
+      if (i < K) G[c * K + i] = g[t];
+    }
   }
   __syncthreads();
   // B3. float64 sweeps from the float32-level angles on G alone (tracked column norms); the right
   // vectors are formed afterwards from T^T
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < K; c += nw) {
-      double s2 = 0.0;
-      for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
-      s2 = warp_sum(s2);
-      if (lane == 0) nrm[c] = s2;
-    }
+  for (int c = warp; c < K; c += nw) {
+    double s2 = 0.0;
+    for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
+    s2 = warp_sum(s2);
+    if (lane == 0) nrm[c] = s2;
   }
   __syncthreads();
-  const int sweeps_b = jacobi_sweeps<double, 2 * JR, false, true, JL / 2>(G, W, sched, K, tol, max_sweeps, &flag, true, nrm);
+  int sweeps_b;
+  if constexpr (JR <= 6)
+    sweeps_b = jacobi_sweeps<double, 2 * JR, false, true, JL / 2>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
+  else
+    sweeps_b = jacobi_sweeps<double, JR, false, true, JL>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
   const int sweeps = sweeps_a + sweeps_b;
   if (threadIdx.x == 0) {
     if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
@@ -376,7 +398,6 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     }
   }
   // column norms (one warp per column)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = warp; c < K; c += nw) {
     double s2 = 0.0;
     for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
@@ -396,10 +417,10 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     Xl[i * K + k] = G[c * K + i] * rnrm[c];
   }
   for (int k = threadIdx.x; k < K; k += blockDim.x) theta[k] = nrm[order[k]];
-  // right vectors of the leading b triplets: w_k = T^T x_k / theta_k = T^T g_k / theta_k^2 (column
+  // right vectors of the leading nv triplets: w_k = T^T x_k / theta_k = T^T g_k / theta_k^2 (column
   // i of T has no entries below its diagonal block); the others are not used by the solver and are
   // left zero
-  const int nv = b < K ? b : K;
+  if (nv > K) nv = K;
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int i = e / K, k = e - i * K;
     double v = 0.0;
@@ -592,7 +613,7 @@ static int jacobi_threads(int K) {
   // one pair per JL lanes, at least 8 warps for the epilogue loops
   int warps = (K / 2 + (32 / JL) - 1) / (32 / JL);
   if (warps < 8) warps = 8;
-  if (warps > 16) warps = 16;   // launch bound 512 threads (K <= 96 needs at most 12 warps)
+  if (warps > 16) warps = 16;   // launch bound 512 threads (K <= 128 needs at most 16 warps)
   return 32 * warps;
 }
 
@@ -613,33 +634,34 @@ bool jacobi_attrs() {
   static int state = 0;  // 1 ok, 2 failed
   std::call_once(once, [] {
     const size_t mx64 =
-        (size_t)(2 * JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
+        (size_t)(JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
     const size_t mxm = (size_t)(2 * JMAXK * JMAXK + JMAXK) * sizeof(float) + (size_t)JMAXK * sizeof(int) +
                        sched_bytes(JMAXK);
     set_smem_attrs<3>(mx64, mxm);
     set_smem_attrs<6>(mx64, mxm);
     set_smem_attrs<9>(mx64, mxm);
     set_smem_attrs<12>(mx64, mxm);
+    set_smem_attrs<16>(mx64, mxm);
     state = cudaGetLastError() == cudaSuccess ? 1 : 2;
   });
   return state == 1;
 }
 
-int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl, double* Wr,
-                     double* res, double tol, int max_sweeps, unsigned int* err, unsigned long long* counters,
-                     cudaStream_t st) {
-  if (!jacobi_attrs()) return 0;  // no launch; the caller's cudaGetLastError check reports the failure
-  const size_t smem = (size_t)(2 * K * K + 2 * K) * sizeof(double) + (size_t)K * sizeof(int) + sched_bytes(K);
+int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta, double* Xl,
+                     double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
+                     unsigned long long* counters, cudaStream_t st) {
+  if (!jacobi_attrs() || K > JMAXK) return 0;  // no launch; the caller's checks report the failure
+  const size_t smem = (size_t)(K * K + 2 * K) * sizeof(double) + (size_t)K * sizeof(int) + sched_bytes(K);
   const int thr = jacobi_threads(K);
   const int rpl = (K + JL - 1) / JL;
-  if (rpl <= 3)
-    k_jacobi_f64<3><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
-  else if (rpl <= 6)
-    k_jacobi_f64<6><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
-  else if (rpl <= 9)
-    k_jacobi_f64<9><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
-  else
-    k_jacobi_f64<12><<<1, thr, smem, st>>>(T, ldT, K, S, b, theta, Xl, Wr, res, tol, max_sweeps, err, counters);
+#define SVT_JF64(JRV) \
+  k_jacobi_f64<JRV><<<1, thr, smem, st>>>(T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err, counters)
+  if (rpl <= 3) SVT_JF64(3);
+  else if (rpl <= 6) SVT_JF64(6);
+  else if (rpl <= 9) SVT_JF64(9);
+  else if (rpl <= 12) SVT_JF64(12);
+  else SVT_JF64(16);
+#undef SVT_JF64
   return 1;
 }
 
@@ -647,8 +669,7 @@ int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int
                            double* Wr, double* res, int nvec, float* wsrc, double tol, int max_sweeps,
                            unsigned int* err, unsigned long long* counters, cudaStream_t st) {
   if (nvec > K) nvec = K;
-  if (nvec > JMAXB) nvec = JMAXB;
-  if (!jacobi_attrs()) return 0;  // no launch; the caller's cudaGetLastError check reports the failure
+  if (!jacobi_attrs() || K > JMAXK) return 0;  // no launch; the caller's checks report the failure
   const size_t smem = (size_t)(2 * K * K + K) * sizeof(float) + (size_t)K * sizeof(int) + sched_bytes(K);
   const int thr = jacobi_threads(K);
   const int rpl = (K + JL - 1) / JL;
@@ -663,8 +684,11 @@ int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int
   else if (rpl <= 9)
     k_jacobi_mixed<9><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err, counters,
                                             tr);
-  else
+  else if (rpl <= 12)
     k_jacobi_mixed<12><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err,
+                                             counters, tr);
+  else
+    k_jacobi_mixed<16><<<1, thr, smem, st>>>(T, ldT, K, theta, Xl, Wr, res, nvec, wsrc, ft, max_sweeps, err,
                                              counters, tr);
   k_ritz_refine<<<nvec, 128, 0, st>>>(T, ldT, K, S, b, wsrc, theta, Xl, Wr, res);
   return 2;

@@ -30,7 +30,7 @@ namespace svt {
 
 static constexpr int ORTH_T = 256;
 static constexpr int OB_MAXB = 32;
-static constexpr int OB_MAXK = 96;
+static constexpr int OB_MAXK = 128;   // nq b <= 128 previous basis columns
 static constexpr double DEFLATE_REL2 = 1e-24;  // squared norm ratio below which a column is dependent
 
 // group of lanes per row: smallest power of two >= b
@@ -47,9 +47,9 @@ static inline int row_group(int b) {
 // spread over many CTAs too.
 // ------------------------------------------------------------------------------------------------
 static constexpr int GRAM_SUB = 8;        // rows staged in shared memory at a time
-static constexpr int GRAM_MAXW = 128;     // (nq + 1) b <= 128
+static constexpr int GRAM_MAXW = 160;     // (nq + 1) b <= 160
 static constexpr int GRAM_MAXE = GRAM_MAXW * 32;
-static constexpr int GRAM_EPT = GRAM_MAXE / ORTH_T;  // entries per thread (16)
+static constexpr int GRAM_EPT = GRAM_MAXE / ORTH_T;  // entries per thread (20)
 
 static int gram_rows_per_cta(int n) {
   int rows = (n + 2 * 152 - 1) / (2 * 152);
@@ -259,9 +259,10 @@ __global__ void __launch_bounds__(ORTH_T)
 k_update_gram(int mode, const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ C,
               const double* __restrict__ R, const double* __restrict__ dinv, double* __restrict__ P, int n, int b,
               int g, int rows_per_cta, double* __restrict__ partial) {
-  __shared__ double sC[OB_MAXK * OB_MAXB];
-  __shared__ double sR[OB_MAXB * OB_MAXB];
-  __shared__ double sD[OB_MAXB];
+  extern __shared__ double sm_upd[];   // C (K x b), then R diag(1 / diag(R)) (b x b), 1 / diag(R)
+  double* sC = sm_upd;
+  double* sR = sC + nq * b * b;
+  double* sD = sR + b * b;
   const int K = nq * b;
   for (int t = threadIdx.x; t < K * b; t += blockDim.x) sC[t] = C[t];
   if (mode == 1) {
@@ -283,7 +284,13 @@ int launch_update_gram(int mode, const double* Q, long long q_stride, int nq, co
   const int g = row_group(b);
   const int rows = gram_rows_per_cta(n);
   const int nblk = (n + rows - 1) / rows;
-  k_update_gram<<<nblk, ORTH_T, 0, st>>>(mode, Q, q_stride, nq, C, R, dinv, P, n, b, g, rows, partial);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_update_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((OB_MAXK * OB_MAXB + OB_MAXB * OB_MAXB + OB_MAXB) * sizeof(double)));
+  });
+  const size_t smem = (size_t)(nq * b * b + b * b + b) * sizeof(double);
+  k_update_gram<<<nblk, ORTH_T, smem, st>>>(mode, Q, q_stride, nq, C, R, dinv, P, n, b, g, rows, partial);
   const int nqg = mode == 0 ? nq : 0;
   const int E = gram_entries(nqg, b, false);
   return 1 + gram_reduce_launch(partial, nblk, E, G, st, Gprev, Tcol, ldT, nqg * b * b, b);

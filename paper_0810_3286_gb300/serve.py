@@ -51,7 +51,7 @@ class Server:
             pass
 
     def submit(self, m: int, n: int, rows=None, cols=None, vals=None, tau: float = 0.0, delta: float = 0.0,
-               eps: float = 1e-4, max_rank: int = 27, precision: str = "fp32", noise_sigma: float = 0.0,
+               eps: float = 1e-4, max_rank: int = 64, precision: str = "fp32", noise_sigma: float = 0.0,
                noise_eps: float = 0.0, dry_run_us: int = 0, dry_run_bytes: int = 0, nnz: int = 0,
                k_max: int = 1000) -> int:
         j = _abi.svt_job()
@@ -82,7 +82,7 @@ class Server:
         """Result dict; with keep_factors also U, d (sigma - tau), V."""
         res = _abi.svt_job_result()
         m, n = self._shapes.pop(job_id, (0, 0))
-        cap = 27
+        cap = 64
         U = np.zeros((m, cap)) if self._keep else None
         d = np.zeros(cap) if self._keep else None
         V = np.zeros((n, cap)) if self._keep else None

@@ -11,7 +11,7 @@ tau = 5 sqrt(m n), delta = 1.2 m n / |Omega|.  Three measurements on the same jo
   * one job at a time (slots = 1) in float32 and in float64 on the first `--single` jobs: mean time
     to eps per job, the plain single-job baseline.
 Every job is capped at K_MAX = 500 SVT iterations; jobs that end without meeting the stopping rule
-(iteration cap, more than 27 singular values above tau, Lanczos stagnation) are counted as failed
+(iteration cap, more than 64 singular values above tau, Lanczos stagnation) are counted as failed
 and left out of the latency percentiles.  Prints one JSON line.  Problem generation happens before
 any timing.
 """
@@ -34,7 +34,7 @@ K_MAX = 500
 
 
 def _submit(srv, p, precision):
-    return srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 27,
+    return srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 64,
                       precision=precision, k_max=K_MAX)
 
 
