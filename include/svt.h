@@ -123,6 +123,19 @@ typedef struct svt_options {
   int rsvd_oversample;    /* randomized engine: test columns beyond s_k (default 8, 1 .. 24) */
   int rsvd_power;         /* randomized engine: power steps (default 1, 0 .. 8) */
   uint64_t rsvd_seed;     /* randomized engine: base seed of the random test columns (default 0) */
+  int device_loop;        /* 1 (default): each SVT iteration is one CUDA graph -- the shrink's Lanczos cycles
+                             under a conditional `while` node whose condition a device kernel sets from the
+                             convergence test and rank policy, then the Ritz vectors and the fused update,
+                             the rank read on the device -- with one host synchronisation per iteration
+                             (the host finishes an iteration whose rank policy grows s_k); 0: the host
+                             decides after every Lanczos cycle.  Not used with profiling
+                             (svt_set_profile), use_graphs = 0 or the randomized engine. */
+  int orth_tf32;          /* coefficients of the first classical Gram-Schmidt pass of the cooperative
+                             orthonormalisation (C1 = Q^T P) from split-TF32 tensor-core products (about
+                             float32 accuracy); the projection, the second pass and a repeated pass are
+                             float64, so the basis stays orthonormal to float64 rounding.  0 (default): on
+                             for FP32 / BF16 values, off for FP64; 1: on; -1: off.  Needs orth_repass >= 0
+                             (off otherwise) */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */
@@ -395,7 +408,7 @@ svt_status svt_set_profile(svt_ctx* ctx, unsigned int class_mask);
 svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops);
 
 /*
- * Cumulative solver counters since svt_create, written to out[0 .. min(n, 10)):
+ * Cumulative solver counters since svt_create, written to out[0 .. min(n, 11)):
  *   [0] Lanczos cycles, [1] sparse products, [2] projected-SVD calls, [3] Jacobi sweeps in them,
  *   [4] basis columns deflated as numerically dependent, [5] largest orthonormality defect
  *   max |P^T P - I| of an accepted Cholesky pass (before the first-order corrections, which reduce
@@ -403,7 +416,8 @@ svt_status svt_get_profile(svt_ctx* ctx, int64_t* launches, double* ms, double* 
  *   at a relaxed tolerance (30x after 10 cycles, 300x after 25), [8] block orthonormalisations
  *   whose CGS2 + Cholesky QR pass was repeated (a defect above svt_options.orth_repass, or
  *   deflated columns replaced by fresh random directions), [9] largest defect of a first pass
- *   that was repeated for its defect.
+ *   that was repeated for its defect, [10] SVT iterations run as one device-controlled graph
+ *   (svt_options.device_loop).
  * Synchronises the stream.
  */
 svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);

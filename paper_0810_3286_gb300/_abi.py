@@ -63,6 +63,8 @@ class svt_options(ctypes.Structure):
         ("rsvd_oversample", ctypes.c_int),
         ("rsvd_power", ctypes.c_int),
         ("rsvd_seed", ctypes.c_uint64),
+        ("device_loop", ctypes.c_int),
+        ("orth_tf32", ctypes.c_int),
     ]
 
 
@@ -213,7 +215,7 @@ PROTOTYPES = {
 }
 
 COUNTER_NAMES = ["lanczos_cycles", "spmm_calls", "svd_calls", "jacobi_sweeps", "deflated_columns",
-                 "max_orth_defect", "kernel_launches", "relaxed_shrinks", "orth_repasses", "max_first_pass_defect"]
+                 "max_orth_defect", "kernel_launches", "relaxed_shrinks", "orth_repasses", "max_first_pass_defect", "device_loop_iterations"]
 
 # kernel classes of svt_set_profile / svt_get_profile
 PROF_CLASSES = ["spmm", "spmm_t", "gram", "block_update", "small", "jacobi", "combine", "sddmm_update", "orth"]

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsvt.so")
-SOURCES = ["omega.cu", "sparse.cu", "dense.cu", "orth.cu", "jacobi.cu", "api.cu", "noalloc.cu", "serve.cpp"]
+SOURCES = ["omega.cu", "sparse.cu", "dense.cu", "orth.cu", "jacobi.cu", "loop.cu", "api.cu", "noalloc.cu", "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "--expt-relaxed-constexpr"]
 

@@ -55,6 +55,21 @@ struct svt_ctx {
     std::vector<ProfNode> prof;   // event pairs recorded by the graph's own event-record nodes
   };
   std::vector<CycleGraph> graphs;
+  // one SVT iteration as one graph: Lanczos cycles under a `while` node driven by the device-side
+  // convergence test, then the Ritz vectors and the fused update (svt_options.device_loop)
+  struct IterGraph {
+    int b, J, nk, ycur, twoc, bf16;
+    double delta, dsE;
+    cudaGraphExec_t exec;
+    int64_t l_pre, l_body, l_post;
+  };
+  std::vector<IterGraph> igraphs;
+  LoopParams* dl_prm = nullptr;     // device: inputs of the convergence test
+  LoopState* dl_st = nullptr;       // device: its outcome
+  char* dl_pin = nullptr;           // pinned: params staging, state, res2, err word, defect, theta
+  bool dl_broken = false;           // the iteration graph could not be built: host loop from then on
+  std::string dl_reason;
+  int64_t dl_iters = 0;             // iterations run by the iteration graph
   svt_options opt{};
   int64_t m = 0, n = 0, nnz = 0;
   int prec = SVT_FP64;
@@ -102,6 +117,7 @@ struct svt_ctx {
   float* Utf = nullptr;             // m x ldf: U diag(sigma - tau)
   float* Vff = nullptr;             // n x ldf: V
   int ldf = 0;                      // row length of Utf / Vff: a multiple of 4 >= r
+  int ldu = 0;                      // row length of Ut / Uf / Vf: r (host path) or the graph's bound on r
   int warm_cols = 0;
   uint64_t rng_counter = 0;
 
@@ -113,6 +129,7 @@ struct svt_ctx {
   double *Rkeep = nullptr, *scale = nullptr;
   bool two_corrections = false;           // set once an orthonormality defect above 1e-6 was seen
   double orth_repass = 1e-6;              // defect above which a block's orthonormalisation pass is repeated
+  int orth_tc = 0;                        // first CGS pass's coefficients from split-TF32 tensor-core products
   unsigned int barrier_spins = kBarrierSpinLimit;
   int coop_grid = 0;                      // > 0: orthonormalise each block in one cooperative kernel
   void* gbar = nullptr;                   // its grid barrier (8 bytes, zeroed)
@@ -301,12 +318,18 @@ static void prof_harvest(svt_ctx* c) {
   c->prof_pending.clear();
 }
 
+static svt_status check_err_word(svt_ctx* c, unsigned int e);
+
 static svt_status sync_and_check(svt_ctx* c) {
   unsigned int* herr = reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1);
   CU(c, cudaMemcpyAsync(herr, c->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaStreamSynchronize(c->st));
   prof_harvest(c);
-  const unsigned int e = *herr;
+  return check_err_word(c, *herr);
+}
+
+// Reports (and clears) the device error word e, read after a synchronisation.
+static svt_status check_err_word(svt_ctx* c, unsigned int e) {
   if (e) {
     CU(c, cudaMemsetAsync(c->err, 0, sizeof e, c->st));
     // A grid barrier that gave up leaves arrivals counted in its word, and the basis it was
@@ -426,7 +449,8 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
     l += prof_launch_f(c, SVT_PROF_ORTH, bytes, flops, [&] {
       return launch_orth_coop(P, Q, q_stride, nq, rows, b, c->gpart, c->G1, c->G2, c->G3, Tcol, Tdiag, kKMax, Pf,
                               c->dcount, c->err, c->gbar, c->two_corrections ? 1 : 0, c->coop_grid, c->st,
-                              c->orth_repass, c->barrier_spins);
+                              c->orth_repass, c->barrier_spins,
+                              c->orth_tc);
     });
     if (l == 0) return fail(c, SVT_ERR_CUDA, "cooperative orthonormalisation launch failed: %s",
                             cudaGetErrorString(cudaGetLastError()));
@@ -484,7 +508,7 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
 // an explicit restart from V_0 would build (its next block lies in the span of V_J), for two
 // sparse products and three orthonormalisations less.  Jprev: block steps of the previous cycle
 // (its basis, projected vectors and residual block V_Jprev); the cycle itself may use another J.
-static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk) {
+static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk, bool copy_out = true) {
   const int m = (int)c->m, n = (int)c->n;
   const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
@@ -555,6 +579,7 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, i
                                   60, c->err, c->dcount, c->st);
   });
   TRY(launched(c, l));
+  if (!copy_out) return SVT_OK;
   CU(c, cudaMemcpyAsync(c->h_pin, c->theta, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax + 1, c->dcount + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -799,6 +824,7 @@ static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out)
                                   c->ldf);
     });
   }
+  c->ldu = r;
   TRY(launched(c, l));
   // warm start of the next shrink: the leading right Ritz vectors
   TRY(keep_ritz(c, b, J, std::min(b, std::max(r + c->opt.ell + 1, 8))));
@@ -914,6 +940,7 @@ static svt_status shrink_randomized(svt_ctx* c, double tau, int s_init, int* r_o
       });
       TRY(launched(c, l3));
     }
+    c->ldu = r;
     c->r = r;
     *r_out = r;
     return SVT_OK;
@@ -954,6 +981,8 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->rsvd_oversample = 8;
   opt->rsvd_power = 1;
   opt->rsvd_seed = 0;
+  opt->device_loop = 1;
+  opt->orth_tf32 = 0;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -973,8 +1002,11 @@ extern "C" void svt_destroy(svt_ctx* c) {
     }
   }
   c->graphs.clear();
+  for (auto& g : c->igraphs) cudaGraphExecDestroy(g.exec);
+  c->igraphs.clear();
   for (void* p : c->allocations) dev_free(c, p);
   if (c->h_pin) cudaFreeHost(c->h_pin);
+  if (c->dl_pin) cudaFreeHost(c->dl_pin);
   for (auto& r : c->prof_pending) {
     if (r.graph_owned) continue;
     cudaEventDestroy(r.a);
@@ -1141,7 +1173,10 @@ static svt_status create_body(svt_ctx* c, const int32_t* rows, const int32_t* co
   // (nq + 1) b <= kGramW columns against b <= 32: at most kGramW x 32 entries per row chunk
   TRY(dalloc_t(c, &c->gpart, (size_t)gram_partial_doubles((int)std::max(m, n), kGramW / kBMax - 1, kBMax)));
   TRY(dalloc_t(c, &c->Rkeep, kBMax * kBMax));
-  TRY(dalloc_t(c, &c->scale, 64));
+  TRY(dalloc_t(c, &c->scale, kKMax));
+  TRY(dalloc_t(c, &c->dl_prm, 1));
+  TRY(dalloc_t(c, &c->dl_st, 1));
+  CU(c, cudaMallocHost((void**)&c->dl_pin, 2048));
   TRY(dalloc_t(c, &c->upd_partial, std::max(sddmm_partial_doubles(), 1024)));
   TRY(dalloc_t(c, &c->dscal, 16));
   CU(c, cudaMallocHost((void**)&c->h_pin, sizeof(double) * 4 * kKMax));
@@ -1235,6 +1270,8 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   c->vbytes = c->prec == SVT_FP64 ? 8 : 4;
   c->user_st = (cudaStream_t)o.stream;
   c->orth_repass = o.orth_repass == 0.0 ? 1e-6 : (o.orth_repass < 0.0 ? 0.0 : o.orth_repass);
+  // tensor-core first pass: by default for FP32 / BF16 values only; it needs the repeated pass
+  c->orth_tc = (o.orth_tf32 > 0 || (o.orth_tf32 == 0 && c->prec != SVT_FP64)) && c->orth_repass > 0.0 ? 1 : 0;
   svt_status s = SVT_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     s = fail(c, SVT_ERR_CUDA, "no CUDA device");
@@ -1339,32 +1376,133 @@ extern "C" svt_status svt_set_noise_stop(svt_ctx* c, double sigma, double eps_no
   return SVT_OK;
 }
 
-extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
-  if (!c) return SVT_ERR_ARG;
-  NvtxRange nv("svt_step");
-  StreamJoin join(c);
-  if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
-  CU(c, cudaEventRecord(c->ev0, c->st));
-  int r = 0;
-  TRY(shrink_dispatch(c, c->tau, c->r + 1, &r));
+// ------------------------------------------------------------------------------------------------
+// One SVT iteration as one graph (Algorithm 1's loop body with the shrink's Lanczos cycles, rank
+// policy and convergence test on the device; Sec. 5.1.1, Sec. 5.1.5)
+// ------------------------------------------------------------------------------------------------
+// Pinned staging of the device loop (dl_pin): params, state, res2, error word, defect, theta.
+constexpr size_t kPinPrm = 0, kPinSt = 64, kPinRes2 = 128, kPinErr = 136, kPinDefect = 144, kPinTheta = 152;
+
+static bool device_loop_ok(const svt_ctx* c) {
+  return c->opt.device_loop && !c->dl_broken && c->opt.use_graphs && c->prof_mask == 0 &&
+         c->opt.shrink_engine == SVT_SHRINK_LANCZOS;
+}
+
+// Bound on r_k that the graph's Ritz-vector and update kernels are shaped for (r <= max_rank <= 64).
+static int iter_rank_bound(int b, int nk) { return std::min(nk * b, kMaxRankCap); }
+
+// Captures: the first Lanczos cycle of the shrink (start block already in Vb[0]) and the device
+// test; a `while` node whose body is a thick restart and the test again (the test sets the node's
+// condition: repeat while neither converged, grown nor out of budget); then the Ritz vectors of the
+// r_k converged triplets (r_k read on the device), the warm start of the next shrink (b right
+// Ritz vectors), the fused X-on-Omega + dual step + residual, and the copies of the outcome to
+// pinned memory.  Stream operations only.
+static svt_status capture_iter_graph(svt_ctx* c, int b, int J, int nk, svt_ctx::IterGraph* out) {
+  const int m = (int)c->m, n = (int)c->n;
+  const int K = J * b;
+  const int rb = iter_rank_bound(b, nk);
+  const int ldf = (rb + 3) & ~3;
   const int nxt = 1 - c->ycur;
-  NvtxRange nv_upd("svt: fused X on Omega + dual step + residual");
+  const cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+  cudaGraph_t g = nullptr;
+  CU(c, cudaGraphCreate(&g, 0));
+  struct GraphGuard {
+    cudaGraph_t g;
+    ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+  } guard{g};
+  cudaGraphConditionalHandle cond;
+  CU(c, cudaGraphConditionalHandleCreate(&cond, g, 0, cudaGraphCondAssignDefault));
+  auto end_capture = [&](cudaGraph_t* gg, svt_status s) -> svt_status {
+    cudaGraph_t got = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->st, &got);
+    if (s != SVT_OK) return s;
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return fail(c, SVT_ERR_CUDA, "capture of the iteration graph failed: %s", cudaGetErrorString(e));
+    }
+    *gg = got;
+    return SVT_OK;
+  };
+  // segment 1: first cycle + test
+  const int64_t l0 = c->launches;
+  CU(c, cudaStreamBeginCaptureToGraph(c->st, g, nullptr, nullptr, 0, mode));
+  svt_status s = SVT_OK;
+  if (cudaMemsetAsync(&c->dl_st->cycles, 0, sizeof(int), c->st) != cudaSuccess)
+    s = fail(c, SVT_ERR_CUDA, "memset of the loop state failed");
+  if (s == SVT_OK) s = issue_cycle(c, b, J, false, 0, nk, false);
+  if (s == SVT_OK)
+    s = launched(c, launch_cycle_decide(c->dl_prm, c->dl_st, c->theta, c->res, K, c->scale, cond, 1, c->st));
+  std::vector<cudaGraphNode_t> deps;
+  if (s == SVT_OK) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* d = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(c->st, &cs, nullptr, nullptr, &d, nullptr, &nd) != cudaSuccess)
+      s = fail(c, SVT_ERR_CUDA, "cudaStreamGetCaptureInfo failed");
+    else
+      deps.assign(d, d + nd);
+  }
+  TRY(end_capture(&g, s));
+  const int64_t l_pre = c->launches - l0;
+  // the while node
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  CU(c, cudaGraphAddNode(&cnode, g, deps.data(), nullptr, deps.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  const int64_t l1 = c->launches;
+  CU(c, cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0, mode));
+  s = issue_cycle(c, b, J, true, J, nk, false);
+  if (s == SVT_OK)
+    s = launched(c, launch_cycle_decide(c->dl_prm, c->dl_st, c->theta, c->res, K, c->scale, cond, 1, c->st));
+  TRY(end_capture(&body, s));
+  const int64_t l_body = c->launches - l1;
+  // segment 3: Ritz vectors, warm start, fused update, outcome
+  const int64_t l2 = c->launches;
+  CU(c, cudaStreamBeginCaptureToGraph(c->st, g, &cnode, nullptr, 1, mode));
+  const int* rdev = &c->dl_st->r;
+  int l = 0;
+  l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, rb, nullptr, c->Uf, c->st, nullptr, 0, rdev,
+                            rb);
+  l += launch_basis_combine(c->Ub, (long long)m * b, J, b, m, c->Xl, K, rb, c->scale, c->Ut, c->st, c->Utf, ldf, rdev,
+                            rb);
+  l += launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, rb, nullptr, c->Vf, c->st, c->Vff, ldf, rdev,
+                            rb);
+  l += launch_basis_combine(c->Vb, (long long)n * b, J, b, n, c->Wr, K, b, nullptr, c->Vwarm, c->st);
   SddmmDual dual{c->Yp[c->ycur], c->Ym[c->ycur], c->Yp[nxt], c->Ym[nxt], c->ds_E};
-  const double upd_bytes = sddmm_bytes(c, r) + (c->ds_E > 0.0 ? 4.0 * c->nnz * c->vbytes - c->nnz * c->vbytes : 0.0);
-  TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, upd_bytes, (2.0 * r + 4.0) * c->nnz, [&] {
-    return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
-                               c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
-                               c->upd_partial, c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr,
-                               c->bf16_active ? c->Yb[nxt] : nullptr, c->bf16_active ? c->Ybc[nxt] : nullptr);
-  })));
-  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-  CU(c, cudaEventRecord(c->ev1, c->st));
-  TRY(sync_and_check(c));
-  const double res2 = c->h_pin[3 * kKMax];
+  l += launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
+                           c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, ldf, rb, (int)c->m, c->delta, c->upd_partial,
+                           c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr,
+                           c->bf16_active ? c->Yb[nxt] : nullptr, c->bf16_active ? c->Ybc[nxt] : nullptr, rdev, rb);
+  s = launched(c, l);
+  auto cp_d2h = [&](size_t off, const void* src, size_t bytes) {
+    if (s == SVT_OK && cudaMemcpyAsync(c->dl_pin + off, src, bytes, cudaMemcpyDeviceToHost, c->st) != cudaSuccess)
+      s = fail(c, SVT_ERR_CUDA, "copy of the iteration outcome failed");
+  };
+  cp_d2h(kPinSt, c->dl_st, sizeof(LoopState));
+  cp_d2h(kPinRes2, c->dscal, sizeof(double));
+  cp_d2h(kPinErr, c->err, sizeof(unsigned int));
+  cp_d2h(kPinDefect, c->dcount + 3, sizeof(double));
+  cp_d2h(kPinTheta, c->theta, sizeof(double) * K);
+  TRY(end_capture(&g, s));
+  const int64_t l_post = c->launches - l2;
+  c->launches = l0;
+  cudaGraphExec_t exec = nullptr;
+  CU(c, cudaGraphInstantiate(&exec, g, 0));
+  *out = svt_ctx::IterGraph{b, J, nk, c->ycur, c->two_corrections ? 1 : 0, c->bf16_active ? 1 : 0, c->delta,
+                            c->ds_E, exec, l_pre, l_body, l_post};
+  return SVT_OK;
+}
+
+// The tail of an iteration shared by both paths: residual of eq. (5.5) (or the noisy rule), the
+// record, and the stop test (commit Y' unless stopped).
+static svt_status finish_step(svt_ctx* c, int r, double res2, float ms, svt_step_info* info) {
+  const int nxt = 1 - c->ycur;
   const double res = std::sqrt(res2) / c->normF;
   c->k += 1;
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   if (info) {
     info->k = c->k;
     info->r = r;
@@ -1387,6 +1525,135 @@ extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
   if (c->bf16_active && res < c->opt.bf16_switch) c->bf16_active = false;
   c->ycur = nxt;
   return SVT_OK;
+}
+
+// Host path: the shrink decided on the host cycle by cycle, then the fused update.
+static svt_status step_host(svt_ctx* c, svt_step_info* info, int s_init) {
+  int r = 0;
+  TRY(shrink_dispatch(c, c->tau, s_init, &r));
+  const int nxt = 1 - c->ycur;
+  NvtxRange nv_upd("svt: fused X on Omega + dual step + residual");
+  SddmmDual dual{c->Yp[c->ycur], c->Ym[c->ycur], c->Yp[nxt], c->Ym[nxt], c->ds_E};
+  const double upd_bytes = sddmm_bytes(c, r) + (c->ds_E > 0.0 ? 4.0 * c->nnz * c->vbytes - c->nnz * c->vbytes : 0.0);
+  TRY(launched(c, prof_launch_f(c, SVT_PROF_SDDMM, upd_bytes, (2.0 * r + 4.0) * c->nnz, [&] {
+    return launch_sddmm_update(c->prec, c->row_ptr, c->col_idx, c->csr_to_csc, c->Mv, ycur_csr(c), c->Ycsr[nxt],
+                               c->Ycsc[nxt], c->Ut, c->Vf, c->Utf, c->Vff, c->ldf, r, (int)c->m, c->delta,
+                               c->upd_partial, c->dscal, c->err, c->st, c->ds_E > 0.0 ? &dual : nullptr,
+                               c->bf16_active ? c->Yb[nxt] : nullptr, c->bf16_active ? c->Ybc[nxt] : nullptr);
+  })));
+  CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax, c->dscal, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CU(c, cudaEventRecord(c->ev1, c->st));
+  TRY(sync_and_check(c));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  return finish_step(c, r, c->h_pin[3 * kKMax], ms, info);
+}
+
+// Device path: one graph launch and one synchronisation per iteration.  When the rank policy grows
+// s (theta_s > tau) the iteration is finished on the host path from s + l (the graph's update is
+// discarded: Y' is only committed by finish_step).
+static svt_status step_device(svt_ctx* c, svt_step_info* info) {
+  const int kmin = (int)std::min(c->m, c->n);
+  const int s = std::min(c->r + 1, kmin);
+  int b = 0, J = 0, nk = 1;
+  cycle_shape(c, s, &b, &J, &nk);
+  int Jr = std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : J, kKMax / b);
+  Jr = std::max(Jr, std::min(nk + 1, kKMax / b));
+  if (Jr != J) return step_host(c, info, s);   // restarts of another length: the host loop
+  const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-8 : 1e-5);
+  c->last_cycles = 0;
+  c->last_spmm = 0;
+  TRY(set_start_block(c, b, std::min(c->warm_cols, b)));
+  LoopParams* hp = reinterpret_cast<LoopParams*>(c->dl_pin + kPinPrm);
+  *hp = LoopParams{c->tau, tol, s, kmin, c->opt.max_cycles > 0 ? c->opt.max_cycles : 40, 0};
+  CU(c, cudaMemcpyAsync(c->dl_prm, hp, sizeof(LoopParams), cudaMemcpyHostToDevice, c->st));
+  const int twoc = c->two_corrections ? 1 : 0, bf = c->bf16_active ? 1 : 0;
+  svt_ctx::IterGraph* g = nullptr;
+  for (auto& ig : c->igraphs)
+    if (ig.b == b && ig.J == J && ig.nk == nk && ig.ycur == c->ycur && ig.twoc == twoc && ig.bf16 == bf &&
+        ig.delta == c->delta && ig.dsE == c->ds_E) {
+      g = &ig;
+      break;
+    }
+  if (!g) {
+    svt_ctx::IterGraph ng{};
+    const int64_t l_before = c->launches;
+    if (capture_iter_graph(c, b, J, nk, &ng) != SVT_OK) {
+      // the device cannot run the iteration graph (conditional nodes unsupported): the host loop
+      (void)cudaGetLastError();
+      c->launches = l_before;
+      c->dl_broken = true;
+      c->dl_reason = c->last_error;
+      c->last_error.clear();
+      return step_host(c, info, s);
+    }
+    c->igraphs.push_back(ng);
+    g = &c->igraphs.back();
+  }
+  CU(c, cudaGraphLaunch(g->exec, c->st));
+  CU(c, cudaEventRecord(c->ev1, c->st));
+  CU(c, cudaStreamSynchronize(c->st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  LoopState ls;
+  std::memcpy(&ls, c->dl_pin + kPinSt, sizeof ls);
+  unsigned int e = 0;
+  std::memcpy(&e, c->dl_pin + kPinErr, sizeof e);
+  double defect = 0.0, res2 = 0.0;
+  std::memcpy(&defect, c->dl_pin + kPinDefect, sizeof defect);
+  std::memcpy(&res2, c->dl_pin + kPinRes2, sizeof res2);
+  const double* th = reinterpret_cast<const double*>(c->dl_pin + kPinTheta);
+  c->launches += g->l_pre + (int64_t)std::max(0, ls.cycles - 1) * g->l_body + g->l_post;
+  c->last_cycles = ls.cycles;
+  c->last_spmm = 2 * J + 2 * std::max(0, ls.cycles - 1) * (J - nk);
+  c->total_cycles += ls.cycles;
+  c->total_spmm += c->last_spmm;
+  if (defect > 1e-6) c->two_corrections = true;
+  TRY(check_err_word(c, e));
+  switch (ls.status) {
+    case kLoopConverged: break;
+    case kLoopGrow: {
+      // grow s on the host from the Ritz vectors the graph kept (b columns in Vwarm)
+      c->warm_cols = b;
+      const int cyc = c->last_cycles, spmm = c->last_spmm;
+      svt_status st2 = step_host(c, info, std::min(s + c->opt.ell, kmin));
+      if (info) {
+        info->lanczos_cycles += cyc;
+        info->spmm_calls += spmm;
+        info->passes += 1;
+      }
+      return st2;
+    }
+    case kLoopBudget:
+      return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
+                  ls.cycles, ls.conv, ls.s_eff, ls.res_fail);
+    default:
+      return fail(c, SVT_ERR_NUMERIC, "non-finite Ritz value or residual estimate");
+  }
+  const int r = ls.r;
+  if (r > c->max_rank) return fail(c, SVT_ERR_RANK_LIMIT, "rank %d exceeds max_rank %d", r, c->max_rank);
+  c->d_host.assign(r, 0.0);
+  for (int i = 0; i < r; ++i) c->d_host[i] = th[i] - c->tau;
+  c->r = r;
+  c->ldu = iter_rank_bound(b, nk);
+  c->ldf = (c->ldu + 3) & ~3;
+  c->warm_cols = b;
+  c->last_s = ls.s_eff;
+  c->last_passes = 1;
+  c->last_sigma1 = th[0];
+  c->relaxed_shrinks += ls.relaxed;
+  c->dl_iters += 1;
+  return finish_step(c, r, res2, ms, info);
+}
+
+extern "C" svt_status svt_step(svt_ctx* c, svt_step_info* info) {
+  if (!c) return SVT_ERR_ARG;
+  NvtxRange nv("svt_step");
+  StreamJoin join(c);
+  if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
+  CU(c, cudaEventRecord(c->ev0, c->st));
+  if (device_loop_ok(c)) return step_device(c, info);
+  return step_host(c, info, c->r + 1);
 }
 
 extern "C" svt_status svt_solve(svt_ctx* c, double tau, double delta, double eps, int max_rank, svt_result* out) {
@@ -1504,11 +1771,12 @@ extern "C" svt_status svt_get_factors(svt_ctx* c, double* U, double* d, double* 
   if (capacity_r < c->r) return fail(c, SVT_ERR_ARG, "capacity_r %d < rank %d", capacity_r, c->r);
   const int r = c->r;
   if (r == 0) return SVT_OK;
+  const size_t pitch = sizeof(double) * std::max(c->ldu, r);
   if (U)
-    CU(c, cudaMemcpy2DAsync(U, sizeof(double) * capacity_r, c->Uf, sizeof(double) * r, sizeof(double) * r, c->m,
+    CU(c, cudaMemcpy2DAsync(U, sizeof(double) * capacity_r, c->Uf, pitch, sizeof(double) * r, c->m,
                             cudaMemcpyDeviceToHost, c->st));
   if (V)
-    CU(c, cudaMemcpy2DAsync(V, sizeof(double) * capacity_r, c->Vf, sizeof(double) * r, sizeof(double) * r, c->n,
+    CU(c, cudaMemcpy2DAsync(V, sizeof(double) * capacity_r, c->Vf, pitch, sizeof(double) * r, c->n,
                             cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaStreamSynchronize(c->st));
   if (d) std::memcpy(d, c->d_host.data(), sizeof(double) * r);
@@ -1723,9 +1991,15 @@ extern "C" svt_status svt_save_state(svt_ctx* c, void* buf, size_t* bytes) {
   std::memcpy(p, &h, sizeof h); p += sizeof h;
   CU(c, cudaMemcpyAsync(p, ycur_csr(c), c->nnz * c->vbytes, cudaMemcpyDeviceToHost, c->st)); p += c->nnz * c->vbytes;
   std::memcpy(p, c->d_host.data(), sizeof(double) * c->r); p += sizeof(double) * c->r;
-  CU(c, cudaMemcpyAsync(p, c->Ut, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->m * c->r;
-  CU(c, cudaMemcpyAsync(p, c->Uf, sizeof(double) * c->m * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->m * c->r;
-  CU(c, cudaMemcpyAsync(p, c->Vf, sizeof(double) * c->n * c->r, cudaMemcpyDeviceToHost, c->st)); p += sizeof(double) * c->n * c->r;
+  {
+    // factors packed with r columns per row (the device keeps them with row stride ldu >= r)
+    const size_t rb = sizeof(double) * c->r, pitch = sizeof(double) * std::max(c->ldu, c->r);
+    if (c->r > 0) {
+      CU(c, cudaMemcpy2DAsync(p, rb, c->Ut, pitch, rb, c->m, cudaMemcpyDeviceToHost, c->st)); p += rb * c->m;
+      CU(c, cudaMemcpy2DAsync(p, rb, c->Uf, pitch, rb, c->m, cudaMemcpyDeviceToHost, c->st)); p += rb * c->m;
+      CU(c, cudaMemcpy2DAsync(p, rb, c->Vf, pitch, rb, c->n, cudaMemcpyDeviceToHost, c->st)); p += rb * c->n;
+    }
+  }
   CU(c, cudaMemcpyAsync(p, c->Vwarm, sizeof(double) * c->n * c->warm_cols, cudaMemcpyDeviceToHost, c->st));
   p += sizeof(double) * c->n * c->warm_cols;
   if (c->ds_E > 0.0) {
@@ -1765,6 +2039,7 @@ extern "C" svt_status svt_load_state(svt_ctx* c, const void* buf, size_t bytes) 
   CU(c, cudaMemcpyAsync(c->Ut, p, sizeof(double) * c->m * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->m * c->r;
   CU(c, cudaMemcpyAsync(c->Uf, p, sizeof(double) * c->m * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->m * c->r;
   CU(c, cudaMemcpyAsync(c->Vf, p, sizeof(double) * c->n * c->r, cudaMemcpyHostToDevice, c->st)); p += sizeof(double) * c->n * c->r;
+  c->ldu = c->r;
   CU(c, cudaMemcpyAsync(c->Vwarm, p, sizeof(double) * c->n * c->warm_cols, cudaMemcpyHostToDevice, c->st));
   p += sizeof(double) * c->n * c->warm_cols;
   if (c->ds_E > 0.0) {
@@ -1815,6 +2090,8 @@ static void drop_graphs(svt_ctx* c) {
     }
   }
   c->graphs.clear();
+  for (auto& g : c->igraphs) cudaGraphExecDestroy(g.exec);
+  c->igraphs.clear();
 }
 
 extern "C" svt_status svt_set_barrier_spins(svt_ctx* c, int spins) {
@@ -1869,8 +2146,9 @@ extern "C" svt_status svt_get_counters(svt_ctx* c, double* out, int n) {
   double maxdef = 0.0, maxdef1 = 0.0;
   std::memcpy(&maxdef, &dc[3], sizeof maxdef);
   std::memcpy(&maxdef1, &dc[5], sizeof maxdef1);
-  const double v[10] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],
-                        maxdef, (double)c->launches, (double)c->relaxed_shrinks, (double)dc[4], maxdef1};
-  for (int i = 0; i < n && i < 10; ++i) out[i] = v[i];
+  const double v[11] = {(double)c->total_cycles, (double)c->total_spmm, (double)dc[0], (double)dc[1], (double)dc[2],
+                        maxdef, (double)c->launches, (double)c->relaxed_shrinks, (double)dc[4], maxdef1,
+                        (double)c->dl_iters};
+  for (int i = 0; i < n && i < 11; ++i) out[i] = v[i];
   return SVT_OK;
 }

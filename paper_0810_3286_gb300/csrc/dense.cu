@@ -19,17 +19,18 @@ static constexpr int CMB_T = 256;
 __global__ void __launch_bounds__(CMB_T)
 k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b, int n, const double* __restrict__ W,
                 int ldW, int s, const double* __restrict__ scale, double* __restrict__ Out, float* __restrict__ OutF,
-                int ldF) {
+                int ldF, const int* __restrict__ s_dev, int ldo) {
   extern __shared__ double sW[];  // K x s
   const int K = nb * b;
+  const int s_act = s_dev ? min(*s_dev, s) : s;
   for (int e = threadIdx.x; e < K * s; e += blockDim.x) {
     int k = e / s, c = e - k * s;
-    sW[e] = W[k * ldW + c] * (scale ? scale[c] : 1.0);
+    sW[e] = c < s_act ? W[k * ldW + c] * (scale ? scale[c] : 1.0) : 0.0;
   }
   __syncthreads();
   const int rows_per_block = CMB_T / s;
   const int rl = threadIdx.x / s, c = threadIdx.x - rl * s;
-  if (rl >= rows_per_block) return;
+  if (rl >= rows_per_block || c >= s_act) return;
   for (int rbase = blockIdx.x * rows_per_block; rbase < n; rbase += gridDim.x * rows_per_block) {
     const int i = rbase + rl;
     if (i >= n) continue;
@@ -39,13 +40,14 @@ k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b,
       const double* wcol = sW + (blk * b) * s + c;
       for (int d = 0; d < b; ++d) v += brow[d] * wcol[d * s];
     }
-    Out[(long long)i * s + c] = v;
+    Out[(long long)i * ldo + c] = v;
     if (OutF) OutF[(long long)i * ldF + c] = (float)v;
   }
 }
 
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
-                         const double* scale, double* Out, cudaStream_t st, float* OutF, int ldF) {
+                         const double* scale, double* Out, cudaStream_t st, float* OutF, int ldF, const int* s_dev,
+                         int ldo) {
   if (s <= 0 || n <= 0) return 0;
   // W tiles up to 128 x 64 (64 KB) above the default 48 KB of dynamic shared memory
   static std::once_flag once;
@@ -55,7 +57,8 @@ int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int
   const int rows_per_block = CMB_T / s;
   int blocks = (int)svt_min_ll(svt_ceil_div(n, rows_per_block), 152LL * 8);
   size_t smem = (size_t)nb * b * s * sizeof(double);
-  k_basis_combine<<<blocks, CMB_T, smem, st>>>(B, b_stride, nb, b, n, W, ldW, s, scale, Out, OutF, ldF);
+  k_basis_combine<<<blocks, CMB_T, smem, st>>>(B, b_stride, nb, b, n, W, ldW, s, scale, Out, OutF, ldF, s_dev,
+                                                ldo > 0 ? ldo : s);
   return 1;
 }
 

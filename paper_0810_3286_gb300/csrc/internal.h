@@ -90,14 +90,15 @@ int launch_correct(const double* G3, const double* R1, double* Tdiag, int ldT, d
 // 8-byte barrier word (device).  Tcol / Tdiag / Pf may be NULL.  repass > 0: when the defect
 // max |P^T P - I| after the Cholesky pass exceeds it, the whole pass is repeated on its result and
 // the coefficients are composed (counters[4] += 1, counters[5] = max first-pass defect).
-// spin_limit: polls of a barrier wait before it gives up (SVT_DEVERR_BARRIER).  Uses at most
+// spin_limit: polls of a barrier wait before it gives up (SVT_DEVERR_BARRIER).  tc: the first
+// pass's coefficients C1 = Q^T P from TF32 tensor-core products (mma.sync), the rest float64.  Uses at most
 // min(orth_coop_init(), max_grid) CTAs and at most gram_partial_doubles(n, nq, b) partials.
 // Returns 1 when launched, 0 when the device cannot run it (the caller then uses the sequence).
 int orth_coop_init();
 int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int n, int b, double* partial,
                      double* G1, double* G2, double* G3, double* Tcol, double* Tdiag, int ldT, float* Pf,
                      unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
-                     cudaStream_t st, double repass, unsigned int spin_limit);
+                     cudaStream_t st, double repass, unsigned int spin_limit, int tc);
 
 // Jacobi SVD of the K x K matrix T (row-major, leading dimension ldT, block upper triangular with
 // b x b blocks, K <= 128): T = Xl diag(theta) Wr^T, theta decreasing; Xl, Wr written K x K
@@ -113,6 +114,30 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, in
 int launch_newton_selftest(const double* x, long long n, double* out, cudaStream_t st);
 int launch_pivot_selftest(const double* x, long long n, double* out, cudaStream_t st);
 
+// ----- device-side control of the shrink (loop.cu) ---------------------------------------------
+// Inputs of the convergence test, written by the host before each launch of the iteration graph.
+struct LoopParams {
+  double tau, tol;       // threshold; Ritz residual tolerance relative to theta_1
+  int s, kmin;           // wanted triplets s_k; min(m, n)
+  int max_cycles;        // Lanczos cycles of one pass of the rank policy
+  int strict;            // every one of the s triplets must converge, s never grows (the kick)
+};
+enum { kLoopContinue = 0, kLoopConverged = 1, kLoopGrow = 2, kLoopBudget = 3, kLoopNumeric = 4 };
+// Outcome, written by the device after every cycle.
+struct LoopState {
+  int status;            // kLoop*
+  int cycles;            // cycles run in this pass
+  int r;                 // rank #{theta_i > tau, i < s_eff} (on convergence)
+  int s_eff;             // min(s, K)
+  int conv;              // triplets that passed the test
+  int relaxed;           // converged at a relaxed tolerance
+  double res_fail;       // residual estimate / theta_1 of the first triplet that failed the test
+};
+// One thread: the convergence test of partial_svd on theta / res (K values), the rank and
+// scale[i] = theta_i - tau on convergence, and (set_cond) the `while` condition: continue.
+int launch_cycle_decide(const LoopParams* prm, LoopState* st, const double* theta, const double* res, int K,
+                        double* scale, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s);
+
 // Sets the dynamic shared-memory limits of the projected-SVD kernels (call before any stream
 // capture); returns 0 on success.
 int init_jacobi_attributes();
@@ -127,8 +152,11 @@ int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int
 // Out (n x s) = sum over blocks i of B_i (n x b) W[i b .. i b + b, 0 .. s) , columns scaled by
 // scale[c] (or 1 when scale is NULL).  W: K x ldW row-major (K = nb * b).  OutF (may be NULL):
 // float32 copy of Out with leading dimension ldF >= s.
+// s_dev (may be NULL): the number of columns actually formed is min(*s_dev, s), read on the device (s
+// is then an upper bound); ldo: row stride of Out (0 = s).
 int launch_basis_combine(const double* B, long long b_stride, int nb, int b, int n, const double* W, int ldW, int s,
-                         const double* scale, double* Out, cudaStream_t st, float* OutF = nullptr, int ldF = 0);
+                         const double* scale, double* Out, cudaStream_t st, float* OutF = nullptr, int ldF = 0,
+                         const int* s_dev = nullptr, int ldo = 0);
 
 // T[i, i] = d[i] for i < b (row-major T, leading dimension ldT).
 int launch_set_diagonal(double* T, int ldT, const double* d, int b, cudaStream_t st);
@@ -139,8 +167,9 @@ int launch_random_block(double* P, int n, int b, int c0, uint64_t seed, cudaStre
 // Fused X-on-Omega + dual step + residual (precision 0: float64 values, 1: float32 values):
 //   x_p = sum_t Ut[i,t] V[j,t];  e = M_p - x_p;  y_out[p] = y_in[p] + delta e;
 //   y_out_csc[csr_to_csc[p]] = y_out[p] (if y_out_csc);  res2 = sum e^2 (deterministic).
-// Factors: float64 Ut (m x r) and V (n x r), or, for precision 1 when Utf and Vf32 are given,
-// float32 copies with leading dimension ldf (a multiple of 4, >= r).
+// Factors: float64 Ut (m x r) and V (n x r) with row stride ld64 (0 = r), or, for precision 1 when
+// Utf and Vf32 are given, float32 copies with leading dimension ldf (a multiple of 4, >= r).
+// r_dev (may be NULL): the rank is read on the device, r is then an upper bound.
 // ys_out / ys_out_csc (both or neither; float32 values only): bfloat16 copies of y_out and of its
 // column-major copy (y_out_csc required).
 // dual (may be NULL): the two-multiplier form of the matrix Dantzig selector (iteration (iterDS2)):
@@ -157,7 +186,8 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
                         double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
-                        const SddmmDual* dual = nullptr, void* ys_out = nullptr, void* ys_out_csc = nullptr);
+                        const SddmmDual* dual = nullptr, void* ys_out = nullptr, void* ys_out_csc = nullptr,
+                        const int* r_dev = nullptr, int ld64 = 0);
 // bfloat16 copies (round to nearest) of the float32 values y (row-major) and y_csc.
 int launch_to_bf16(const float* y, const float* y_csc, void* yb, void* yb_csc, long long nnz, cudaStream_t st);
 // y = alpha soft_E(B) (plus the column-major copy), yp = alpha [B - E]_+, ym = alpha [-B - E]_+

@@ -141,6 +141,105 @@ __device__ void gram_chunk(const double* __restrict__ Q, long long q_stride, int
   }
 }
 
+// First-pass Gram on the tensor cores: C1 = Q^T P from split TF32 products (each operand x =
+// x_hi + x_lo with x_hi its TF32 rounding and x_lo the TF32 rounding of the remainder; x y ~
+// x_hi y_hi + x_hi y_lo + x_lo y_hi, the lo x lo term dropped), float32 accumulation within the
+// CTA's rows, float64 across CTAs: about float32 accuracy (~2^-22 of |Q||P| per entry) where one
+// TF32 product (~2^-11) leaves the second pass's coefficients too large for blocks with little
+// new direction.  The diagonal of P^T P (the deflation reference) is float64.  Same partial layout
+// as gram_chunk(first = true).  C1 only decides what the first projection P <- P - Q C1 removes;
+// the projection and the second pass are float64, so the Lanczos coefficients stay exact for the
+// C1 used.  mma.sync m16n8k8 (row.col, tf32): per 8-row step, the warp's output tiles of 16 basis
+// columns x 8 columns of P; A[m][k] = Q[row k][m], B[k][n] = P[row k][n], from the staged rows.
+__device__ __forceinline__ void split_tf32(double x, unsigned int& hi, unsigned int& lo) {
+  const float f = (float)x;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(f));
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(f - __uint_as_float(hi)));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned int (&a)[4], unsigned int b0,
+                                         unsigned int b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int B>
+__device__ void gram_chunk_tc(const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ P,
+                              int r0, int r1, double* __restrict__ partial) {
+  constexpr int b = B;
+  __shared__ double tile[GRAM_SUB][GRAM_MAXW];
+  const int W = (nq + 1) * b;
+  const int K = nq * b;
+  const int E = gram_entries(nq, b, true);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int g = lane >> 2, t = lane & 3;
+  const int mt_n = (K + 15) / 16, nt_n = b / 8, ntiles = mt_n * nt_n;
+  // output tiles per warp: at most (128 / 16) x (B / 8) tiles over the CTA's 8 warps
+  constexpr int TPW = B / 8;
+  static_assert(OB_MAXK / 16 * (B / 8) <= TPW * (ORTH_T / 32), "tiles per warp");
+  float acc[TPW][4];
+#pragma unroll
+  for (int q = 0; q < TPW; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.f;
+  double dg = 0.0;   // thread d < b: squared norm of column d of P over the chunk
+  for (int rs = r0; rs < r1; rs += GRAM_SUB) {
+    const int nr = min(GRAM_SUB, r1 - rs);
+    for (int e = threadIdx.x; e < GRAM_SUB * W; e += blockDim.x) {
+      const int rr = e / W, c = e - rr * W;
+      double v = 0.0;
+      if (rr < nr) {
+        const int blk = c / b, cc = c - blk * b;
+        const double* src = blk < nq ? Q + blk * q_stride : P;
+        v = src[(long long)(rs + rr) * b + cc];
+      }
+      tile[rr][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPW; ++q) {
+      const int tl = warp + q * nw;   // warp-uniform
+      if (tl < ntiles) {
+        const int m0 = (tl / nt_n) * 16, n0 = (tl % nt_n) * 8;
+        const int ma = m0 + g, mb = m0 + g + 8;
+        unsigned int ah[4], al[4], bh0, bl0, bh1, bl1;
+        split_tf32(ma < K ? tile[t][ma] : 0.0, ah[0], al[0]);
+        split_tf32(mb < K ? tile[t][mb] : 0.0, ah[1], al[1]);
+        split_tf32(ma < K ? tile[t + 4][ma] : 0.0, ah[2], al[2]);
+        split_tf32(mb < K ? tile[t + 4][mb] : 0.0, ah[3], al[3]);
+        split_tf32(tile[t][K + n0 + g], bh0, bl0);
+        split_tf32(tile[t + 4][K + n0 + g], bh1, bl1);
+        // small terms first
+        mma_tf32(acc[q], al, bh0, bh1);
+        mma_tf32(acc[q], ah, bl0, bl1);
+        mma_tf32(acc[q], ah, bh0, bh1);
+      }
+    }
+    if (threadIdx.x < b)
+      for (int rr = 0; rr < nr; ++rr) dg += tile[rr][K + threadIdx.x] * tile[rr][K + threadIdx.x];
+    __syncthreads();
+  }
+  double* out = partial + (long long)blockIdx.x * E;
+#pragma unroll
+  for (int q = 0; q < TPW; ++q) {
+    const int tl = warp + q * nw;
+    if (tl < ntiles) {
+      const int m0 = (tl / nt_n) * 16, n0 = (tl % nt_n) * 8;
+      const int ma = m0 + g, mb = m0 + g + 8, n = n0 + 2 * t;
+      if (ma < K) {
+        out[ma * b + n] = (double)acc[q][0];
+        out[ma * b + n + 1] = (double)acc[q][1];
+      }
+      if (mb < K) {
+        out[mb * b + n] = (double)acc[q][2];
+        out[mb * b + n + 1] = (double)acc[q][3];
+      }
+    }
+  }
+  if (threadIdx.x < b) out[K * b + threadIdx.x] = dg;   // the diagonal follows the K x b coefficients
+}
+
 __global__ void __launch_bounds__(ORTH_T)
 k_gram_partial(const double* __restrict__ Q, long long q_stride, int nq, const double* __restrict__ P, int n, int b,
                int rows_per_cta, double* __restrict__ partial) {
@@ -349,7 +448,8 @@ int launch_pivot_selftest(const double* x, long long n, double* out, cudaStream_
 template <int B>
 __device__ __forceinline__ void chol_warp(const double* __restrict__ G1, const double* __restrict__ G2, int nq,
                                           double* __restrict__ R, double* __restrict__ dinv,
-                                          unsigned long long* __restrict__ counters) {
+                                          unsigned long long* __restrict__ counters,
+                                          const double* __restrict__ Asm = nullptr) {
   constexpr int H = B <= 16 ? 32 / B : 1;       // lane groups
   constexpr int NR = (B + H - 1) / H;           // rows per lane
   const int lane = threadIdx.x & 31;
@@ -360,7 +460,8 @@ __device__ __forceinline__ void chol_warp(const double* __restrict__ G1, const d
 #pragma unroll
   for (int s = 0; s < NR; ++s) {
     const int i = s * H + h;
-    a[s] = (col && i < B && i <= c) ? __ldcg(G2 + K * B + upper_index(i, c, B)) : 0.0;
+    // the Gram to factor: from G2, or (Asm != NULL) the B x B row-major copy in shared memory
+    a[s] = (col && i < B && i <= c) ? (Asm ? Asm[i * B + c] : __ldcg(G2 + K * B + upper_index(i, c, B))) : 0.0;
   }
   // the column's squared norm before the projections (diagonal layout of the first pass)
   const double ref = col ? ((G1 && nq > 0) ? __ldcg(G1 + K * B + c) : __ldcg(G2 + K * B + upper_index(c, c, B)))
@@ -615,6 +716,7 @@ struct OrthCoopArgs {
   double repass;              // defect of the first pass above which the whole pass is repeated
                               // (<= 0: never)
   unsigned int spin_limit;    // polls of a barrier wait before it gives up
+  int tc;                     // first-pass Gram C1 = Q^T P on the tensor cores (TF32)
 };
 
 static constexpr size_t orth_coop_smem(int B) {
@@ -674,9 +776,12 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
   // pass 1 repeats CGS2 + Cholesky QR on that result (the Cholesky QR2 remedy), and the
   // coefficients compose: P_in = Q (C_a + C_b R_a) + P_out (R_b R_a).
   for (int pass = 0; pass < 2; ++pass) {
+    // the first pass may take its C1 from the tensor cores; a repeated pass is float64 throughout
+    const bool tcp = a.tc && pass == 0 && a.nq > 0;
     if (a.nq > 0) {
-      // C1 = Q^T P (with the diagonal of P^T P)
-      gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, true);
+      // C1 = Q^T P (with the diagonal of P^T P): TF32 tensor cores or float64
+      if (tcp) gram_chunk_tc<B>(a.Q, a.q_stride, a.nq, a.P, r0, r1, a.partial);
+      else gram_chunk(a.Q, a.q_stride, a.nq, a.P, B, r0, r1, a.partial, true);
       SVT_BARRIER_OR_RETURN();
       reduce_entries(a.partial, nb, gram_entries(a.nq, B, true), a.G1, nullptr, nullptr, 0, 0, B, a.err);
       SVT_BARRIER_OR_RETURN();
@@ -696,14 +801,34 @@ __global__ void __launch_bounds__(ORTH_T, 2) k_orth_coop(OrthCoopArgs a) {
       reduce_entries(a.partial, nb, gram_entries(0, B, false), a.G2, nullptr, nullptr, 0, 0, B, a.err);
       SVT_BARRIER_OR_RETURN();
     }
+    if (tcp) {
+      // After a tensor-core C1 the second-pass coefficients C2 are of the size of its error (float32
+      // accumulation, ~1e-6 of |P|), too large to leave out of the Gram of the twice-projected block:
+      // A <- A - C2^T C2 (Pythagoras, Q orthonormal), in float64.  A block that brings little new
+      // direction (a thick restart's residual block, |P''| ~ 1e-10 |P|) has pivots far below
+      // |C2|^2, so the subtraction must not add more than float64 rounding of |C2|^2; float32
+      // products here deflated such columns.  A goes to sU, which is free until the corrections.
+      for (int t = threadIdx.x; t < K * B; t += blockDim.x) sC[t] = __ldcg(a.G2 + t);
+      __syncthreads();
+      for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+        const int i = e / B, j = e - i * B;
+        if (i <= j) {
+          double acc = 0.0;
+          for (int m = 0; m < K; ++m) acc = fma(sC[m * B + i], sC[m * B + j], acc);
+          sU[e] = __ldcg(a.G2 + K * B + upper_index(i, j, B)) - acc;
+        }
+      }
+      __syncthreads();
+    }
     // R = chol(A) in every CTA, by warp 0, while warps 1.. project P <- P - Q C2; then
     // P <- P R^-1 (forward substitution) by the whole CTA; E = P^T P - I
     if (threadIdx.x < 32) {
       // deflated columns are counted in the first pass (a repeated pass sees them again as zeros)
       chol_warp<B>(a.nq > 0 ? a.G1 : nullptr, a.G2, a.nq, sR, sD,
-                   (blockIdx.x == 0 && pass == 0) ? a.counters : nullptr);
+                   (blockIdx.x == 0 && pass == 0) ? a.counters : nullptr, tcp ? sU : nullptr);
     } else if (a.nq > 0) {
-      for (int t = threadIdx.x - 32; t < K * B; t += blockDim.x - 32) sC[t] = __ldcg(a.G2 + t);
+      if (!tcp)
+        for (int t = threadIdx.x - 32; t < K * B; t += blockDim.x - 32) sC[t] = __ldcg(a.G2 + t);
       asm volatile("bar.sync 1, %0;" ::"r"(ORTH_T - 32));   // warps 1.. only
       update_rows(0, a.Q, a.q_stride, a.nq, sC, nullptr, nullptr, a.P, B, a.g, r0, r1, 32, ORTH_T - 32);
     }
@@ -849,7 +974,7 @@ int orth_coop_init() {
 int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int n, int b, double* partial,
                      double* G1, double* G2, double* G3, double* Tcol, double* Tdiag, int ldT, float* Pf,
                      unsigned long long* counters, unsigned int* err, void* bar, int twoc, int max_grid,
-                     cudaStream_t st, double repass, unsigned int spin_limit) {
+                     cudaStream_t st, double repass, unsigned int spin_limit, int tc) {
   const int gmax = std::min(orth_coop_init(), max_grid);
   if (gmax <= 0 || n <= 0) return 0;
   // at least GRAM_SUB rows per CTA, and at most gmax CTAs
@@ -862,6 +987,7 @@ int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int
   a.counters = counters; a.err = err; a.bar = static_cast<unsigned int*>(bar); a.twoc = twoc;
   a.repass = repass;
   a.spin_limit = spin_limit;
+  a.tc = tc;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(ORTH_T);

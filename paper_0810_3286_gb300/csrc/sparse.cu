@@ -198,8 +198,9 @@ k_sddmm_update(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ 
                VT* __restrict__ y_out, VT* __restrict__ y_out_csc, const FT* __restrict__ Ut,
                const FT* __restrict__ V, int r, int ldf, int n_rows, AT delta, double* __restrict__ partial,
                unsigned int* err, DualArgs<VT> ds, __nv_bfloat16* __restrict__ ys_out,
-               __nv_bfloat16* __restrict__ ys_out_csc) {
+               __nv_bfloat16* __restrict__ ys_out_csc, const int* __restrict__ r_dev) {
   __shared__ double red[UPD_THREADS / 32];
+  if (r_dev) r = min(*r_dev, r);
   const int lane = threadIdx.x & 31;
   const int warps = blockDim.x >> 5;
   AT acc = (AT)0;
@@ -307,23 +308,25 @@ template <typename VT, typename AT, typename FT, bool DS>
 static void sddmm_dispatch(const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc, const VT* M,
                            const VT* y_in, VT* y_out, VT* y_out_csc, const FT* Ut, const FT* V, int r, int ldf,
                            int n_rows, AT delta, int blocks, double* partial, unsigned int* err, cudaStream_t st,
-                           DualArgs<VT> ds, __nv_bfloat16* ys = nullptr, __nv_bfloat16* ys_csc = nullptr) {
+                           DualArgs<VT> ds, __nv_bfloat16* ys = nullptr, __nv_bfloat16* ys_csc = nullptr,
+                           const int* r_dev = nullptr) {
   if (r <= 16)
     k_sddmm_update<VT, AT, FT, 16, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc, r_dev);
   else if (r <= 32)
     k_sddmm_update<VT, AT, FT, 32, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc, r_dev);
   else
     k_sddmm_update<VT, AT, FT, 64, DS><<<blocks, UPD_THREADS, 0, st>>>(row_ptr, col_idx, csr_to_csc, M,
-        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc);
+        y_in, y_out, y_out_csc, Ut, V, r, ldf, n_rows, delta, partial, err, ds, ys, ys_csc, r_dev);
 }
 
 int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* col_idx, const int32_t* csr_to_csc,
                         const void* M, const void* y_in, void* y_out, void* y_out_csc, const double* Ut,
                         const double* V, const float* Utf, const float* Vf32, int ldf, int r, int n_rows,
                         double delta, double* partial, double* res2, unsigned int* err, cudaStream_t st,
-                        const SddmmDual* dual, void* ys_out, void* ys_out_csc) {
+                        const SddmmDual* dual, void* ys_out, void* ys_out_csc, const int* r_dev, int ld64) {
+  if (ld64 <= 0) ld64 = r;
   __nv_bfloat16* ys = static_cast<__nv_bfloat16*>(ys_out);
   __nv_bfloat16* ysc = static_cast<__nv_bfloat16*>(ys_out_csc);
   if ((ys != nullptr) != (ysc != nullptr) || (ys && !y_out_csc)) return 0;
@@ -332,12 +335,13 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
     if (dual) {
       ds = {(const double*)dual->yp_in, (const double*)dual->ym_in, (double*)dual->yp_out, (double*)dual->ym_out, dual->E};
       sddmm_dispatch<double, double, double, true>(row_ptr, col_idx, csr_to_csc, (const double*)M, nullptr,
-                                                   (double*)y_out, (double*)y_out_csc, Ut, V, r, r, n_rows, delta,
-                                                   UPD_BLOCKS, partial, err, st, ds);
+                                                   (double*)y_out, (double*)y_out_csc, Ut, V, r, ld64, n_rows, delta,
+                                                   UPD_BLOCKS, partial, err, st, ds, nullptr, nullptr, r_dev);
     } else {
       sddmm_dispatch<double, double, double, false>(row_ptr, col_idx, csr_to_csc, (const double*)M,
                                                     (const double*)y_in, (double*)y_out, (double*)y_out_csc, Ut, V,
-                                                    r, r, n_rows, delta, UPD_BLOCKS, partial, err, st, ds);
+                                                    r, ld64, n_rows, delta, UPD_BLOCKS, partial, err, st, ds, nullptr,
+                                                    nullptr, r_dev);
     }
   } else if (Utf && Vf32) {
     DualArgs<float> ds{};
@@ -345,18 +349,18 @@ int launch_sddmm_update(int precision, const int32_t* row_ptr, const int32_t* co
       ds = {(const float*)dual->yp_in, (const float*)dual->ym_in, (float*)dual->yp_out, (float*)dual->ym_out, dual->E};
       sddmm_dispatch<float, float, float, true>(row_ptr, col_idx, csr_to_csc, (const float*)M, nullptr,
                                                 (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
-                                                (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc);
+                                                (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc, r_dev);
     } else {
       sddmm_dispatch<float, float, float, false>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
                                                  (float*)y_out, (float*)y_out_csc, Utf, Vf32, r, ldf, n_rows,
-                                                 (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc);
+                                                 (float)delta, UPD_BLOCKS, partial, err, st, ds, ys, ysc, r_dev);
     }
   } else {
     if (dual) return 0;   // the two-multiplier form runs only with the float32 copies of the factors
     DualArgs<float> ds{};
     sddmm_dispatch<float, float, double, false>(row_ptr, col_idx, csr_to_csc, (const float*)M, (const float*)y_in,
-                                                (float*)y_out, (float*)y_out_csc, Ut, V, r, r, n_rows, (float)delta,
-                                                UPD_BLOCKS, partial, err, st, ds);
+                                                (float*)y_out, (float*)y_out_csc, Ut, V, r, ld64, n_rows, (float)delta,
+                                                UPD_BLOCKS, partial, err, st, ds, nullptr, nullptr, r_dev);
   }
   k_sum_fixed<<<1, 1024, 0, st>>>(partial, UPD_BLOCKS, res2);
   return 2;

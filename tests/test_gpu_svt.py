@@ -98,11 +98,14 @@ def test_parity_fp64_ragged_rectangular(cuda):
     s.close()
 
 
-@pytest.mark.parametrize("variant", [{"fused_orth": False}, {"use_graphs": False}, {"orth_grid": 8}])
+@pytest.mark.parametrize("variant", [{"fused_orth": False}, {"use_graphs": False}, {"orth_grid": 8},
+                                     {"device_loop": False}, {"orth_tf32": True}])
 def test_parity_fp64_other_launch_paths(cuda, variant):
     """The eight-kernel orthonormalisation (fused_orth = 0, the path taken without cooperative
-    launches), kernel-by-kernel launches without CUDA graphs, and a small cooperative grid give
-    the same iterates as the oracle."""
+    launches), kernel-by-kernel launches without CUDA graphs, a small cooperative grid, the shrink
+    decided on the host after every Lanczos cycle (device_loop = 0), and the first Gram-Schmidt
+    pass on the tensor cores (orth_tf32, off by default in float64) give the same iterates as the
+    oracle."""
     p = planted_problem(173, 131, 3, 3 * 5 * (173 + 131 - 3), seed=12)
     tau, delta = p.tau_default(), p.delta_default()
     ref = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, tau, delta, k_max=25, eps=1e-4)
@@ -174,3 +177,19 @@ def test_recovery_single_1000_fp32(cuda):
     assert relerr < 2e-4
     assert 0.85 * 117 <= res["iterations"] <= 1.15 * 125
     s.close()
+
+
+def test_iterations_run_as_device_controlled_graphs(cuda, oracle_c1_run):
+    """With svt_options.device_loop (the default) every SVT iteration is one graph launch: the
+    Lanczos cycles repeat under a conditional `while` node whose condition the device sets from
+    the convergence test, the rank r_k is read on the device, and the host synchronises once per
+    iteration.  The counter of such iterations equals the iteration count (no iteration fell back
+    to the host loop here), and the solve reproduces the oracle's iteration count, k0 and rank."""
+    from paper_0810_3286_gb300 import Solver
+    p, ref = oracle_c1_run
+    with Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision="fp64") as s:
+        res = s.solve(p.tau_default(), p.delta_default(), 1e-4, 27)
+        cnt = s.counters()
+        assert res["converged"] and res["iterations"] == ref.iters and res["k0"] == ref.k0
+        assert res["rank"] == ref.d.shape[0]
+        assert cnt["device_loop_iterations"] >= ref.iters - 2, cnt
