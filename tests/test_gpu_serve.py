@@ -98,3 +98,43 @@ def test_orth_grid_cap_same_solution(cuda):
     assert r0["converged"] and r1["converged"] and r0["rank"] == r1["rank"] == 10
     assert abs(r0["iterations"] - r1["iterations"]) <= 1
     assert np.linalg.norm(X1 - X0) <= 1e-3 * np.linalg.norm(X0)
+
+
+_ORACLE_RUNS = []   # the oracle's solves of the three jobs, shared by both precisions
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-5), ("fp32", 1e-3)])
+def test_mix_against_oracle_rectangular(cuda, precision, bound):
+    """Rectangular jobs of the serving distribution (m != n, rank 5 - 12, |Omega| = c r (m + n - r)
+    with c in [5.5, 6]) run as a mix of concurrent jobs in the server, each compared with the float64
+    sparse-tier oracle run alone on the same job: the same stopping iteration (float64), X on Omega
+    within the per-iterate bound of the path (1e-5 float64, 1e-3 float32) at the final iterate, and
+    ||X - X_oracle||_F / ||X_oracle||_F (closed form from the factors) within 1e-3."""
+    from oracle import svt_sparse
+    from oracle.sparse import sample_X
+    from paper_0810_3286_gb300.serve import Server
+    jobs = [serving_job(1300 + i, n_range=(500, 700), rank_range=(5, 12), c_range=(5.5, 6.0)) for i in range(3)]
+    assert any(p.n1 != p.n2 for p in jobs)
+    if not _ORACLE_RUNS:
+        _ORACLE_RUNS.extend(svt_sparse.svt(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(),
+                                           k_max=600, keep_trace=False) for p in jobs)
+    refs = _ORACLE_RUNS
+    assert all(r.converged for r in refs)
+    with Server(slots=3, keep_factors=True) as srv:
+        ids = [srv.submit(p.n1, p.n2, p.rows, p.cols, p.vals, p.tau_default(), p.delta_default(), 1e-4, 64,
+                          precision=precision, k_max=600) for p in jobs]
+        out = [srv.wait(i) for i in ids]
+    for p, ref, o in zip(jobs, refs, out):
+        assert o["status"] == 0, (p.n1, p.n2, p.r, o)
+        if precision == "fp64":
+            assert o["iterations"] == ref.iters, (o["iterations"], ref.iters)
+        else:
+            assert abs(o["iterations"] - ref.iters) <= 2, (o["iterations"], ref.iters)
+        assert o["rank"] == ref.d.shape[0] == p.r
+        x = sample_X(p.rows, p.cols, o["U"] * o["d"], o["V"])
+        x_ref = sample_X(p.rows, p.cols, ref.U * ref.d, ref.V)
+        assert np.linalg.norm(x - x_ref) <= bound * np.linalg.norm(x_ref)
+        # ||X - X_ref||_F from the factors: ||X||^2 + ||X_ref||^2 - 2 <X, X_ref>
+        G = (o["U"].T @ ref.U) * np.outer(o["d"], ref.d) * (o["V"].T @ ref.V)
+        nx, nr = float(np.sum(o["d"] ** 2)), float(np.sum(ref.d ** 2))
+        assert np.sqrt(max(nx + nr - 2 * G.sum(), 0.0) / nr) <= 1e-3
