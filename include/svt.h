@@ -438,10 +438,13 @@ svt_status svt_get_counters(svt_ctx* ctx, double* out, int n);
  *   Ut, V               m x r and n x r float64 factors (Ut = U diag(d)), 0 <= r <= 64
  *   y_in, y_out         nnz float64 each, distinct buffers: y_out = y_in + delta (M - x)
  *   res2                host pointer: sum over Omega of (M - x)^2
- *   stream              cudaStream_t (NULL = default stream); the call waits for its own work
+ *   stream              cudaStream_t (NULL = default stream); the call synchronises this stream
+ *                       (cudaStreamSynchronize) before it returns, to read res2
  * Arithmetic is float64, the kernel of svt_sddmm_update on a float64 context.
  * The first call on each device looks up the device address of the scratch array (once per
- * device, with that device current); make that first call before any stream capture.  Every call
+ * device, with that device current; again after cudaDeviceReset has replaced the device's
+ * context, which the call detects from the current context's id); make that first call before
+ * any stream capture.  Every call
  * on a device shares the array and the array keeps the last call's contents; each call writes
  * every entry it reads, so nothing needs clearing, but calls whose device work overlaps (for
  * instance on different streams) race on it.  Errors: SVT_ERR_ARG, SVT_ERR_CUDA, SVT_ERR_NUMERIC;

@@ -7,6 +7,7 @@
 // and cudaFree would stall other work.  This entry point needs no allocation: the caller passes
 // every input and output, and the only scratch (one partial sum per CTA and the final sum) lives
 // in a file-scope __device__ array that every GPU loading this library holds until process exit.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -31,7 +32,37 @@ namespace {
 
 std::mutex g_mu;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};   // id of the context the address belongs to
 thread_local std::string g_noalloc_error;
+
+// Driver entry points reached through the runtime (the library does not link libcuda): the id of
+// the current context tells a cached address from one that died with its context (cudaDeviceReset
+// destroys the primary context and the module with it; the next context loads it anew).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    (void)cudaGetLastError();
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 svt_status noalloc_fail(svt_status s, const char* msg, cudaError_t e = cudaSuccess) {
   char buf[384];
@@ -43,18 +74,22 @@ svt_status noalloc_fail(svt_status s, const char* msg, cudaError_t e = cudaSucce
 
 // Device address of the scratch array on the current device.  In host code the array's name is a
 // host-side stand-in, not a device address, so it is looked up once per device with that device
-// current.
+// current, and again when the device's current context is no longer the one the address was
+// taken in (after cudaDeviceReset).
 svt_status scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(SVT_ERR_CUDA, "cudaGetDevice failed", e);
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(SVT_ERR_ARG, "device index out of range");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) return noalloc_fail(SVT_ERR_CUDA, "cudaGetSymbolAddress of the scratch failed", e);
     g_scratch_addr[dev] = static_cast<double*>(p);
+    // the lookup made the device's primary context current if no context was
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return SVT_OK;

@@ -2,7 +2,8 @@
 callers that cannot call cudaMalloc (device memory owned by another pool, or a loop that cannot
 afford the synchronisation of an allocation).  Its output must match svt_sddmm_update, the
 entry point that works through a context, on two calls in a row (the second call reuses the
-static scratch the first one left behind).
+static scratch the first one left behind), and the float64 oracle's X-on-Omega and dual step
+(oracle.sparse.sample_X, oracle.sparse.dual_update: Y^k = Y^{k-1} + delta P_Omega(M - X^k)).
 
 This file is collected last so that a run that stops at the first failure has run every other
 test before it; it also passes when run alone in a fresh process.
@@ -12,6 +13,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle.sparse import dual_update, sample_X
 from svt_inputs import random_dense, random_sparse_pattern
 
 pytestmark = pytest.mark.gpu
@@ -50,6 +52,11 @@ def test_noalloc_matches_context_entry_point_twice(cuda):
         assert np.all(np.isfinite(a)), "call %d left entries unwritten" % call
         assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(b), call
         assert abs(res_na - res_ref) <= 1e-12 * res_ref, (call, res_na, res_ref)
+        # the oracle, on the same row-major entries: float64 sums of r <= 23 products reordered
+        y_or, res_or = dual_update(y_in.cpu().numpy(), mvals,
+                                   sample_X(rows, cols, Ut.cpu().numpy(), V.cpu().numpy()), delta)
+        assert np.linalg.norm(a - y_or) <= 1e-12 * np.linalg.norm(y_or), call
+        assert abs(res_na - res_or) <= 1e-12 * res_or, (call, res_na, res_or)
     s.close()
 
 
