@@ -168,6 +168,26 @@ typedef struct svt_result {
 /* Fills *opt with the defaults listed above. */
 void svt_default_options(svt_options* opt);
 
+/* Options of svt_batch_solve. */
+typedef struct svt_batch_options {
+  int spmm_grid;          /* CTAs of the persistent batched sparse-product launches (0: 16 per SM) */
+  int update_grid;        /* CTAs of the persistent batched update launches (0: 8 per SM) */
+  int autotune;           /* 1: the warps per segment of every batched sparse product (1, 2, 4 or 8) are
+                             timed on the first product of each class (precision, block width,
+                             direction, mean segment length rounded to a power of two) and the fastest
+                             is kept for the process; 0 (default): the fixed rule of the solo path */
+  int concurrent;         /* 1 (default): each job's own kernels (orthonormalisations, projected SVDs, Ritz
+                             vectors) run on its library stream, the batched launches on a stream of the
+                             batch, ordered by events, and each job's cooperative orthonormalisation gets
+                             max(16, 2 SMs / n) CTAs so that the jobs' kernels overlap on the GPU; 0: all
+                             work in issue order on the first job's stream with the solo launch shapes,
+                             so that with autotune = 0 every iterate equals the job's solo iterate (shrink
+                             decided on the host) */
+} svt_batch_options;
+
+/* Fills *opt with the batch defaults. */
+void svt_batch_default_options(svt_batch_options* opt);
+
 /*
  * Builds a context for one completion problem: stores Omega (Sec. 2.2: Y^k vanishes off Omega,
  * so only Omega is ever stored) in row-major (CSR) and column-major (CSC) order with the
@@ -270,6 +290,27 @@ svt_status svt_solve(svt_ctx* ctx, double tau, double delta, double eps, int max
  * Errors: SVT_ERR_ARG (NULL ctx, tau not positive and finite, context not configured).
  */
 svt_status svt_set_tau(svt_ctx* ctx, double tau);
+
+/*
+ * Batched solve: Algorithm 1 (Sec. 5.1.5) for n independent completion problems at once (the paper
+ * solves one problem at a time; this is the batched form of its iteration).  jobs: n distinct
+ * contexts (1 <= n <= 32), all with the same value precision (FP64 or FP32; not BF16), the Lanczos
+ * shrink engine, no noise stop and no Dantzig selector.  tau, delta: n values each, or NULL (a zero
+ * or NULL entry takes the job's default, as in svt_configure); eps, max_rank: common to all jobs.
+ * Each job is configured (kick of Sec. 5.1.3), then all unfinished jobs advance one SVT iteration
+ * at a time in lockstep: the Lanczos cycles of their shrinks run together, and the sparse products
+ * of all jobs at the same block step, and the fused updates of all jobs, are one persistent launch
+ * each over the ragged job list.  Every job follows its own rank policy, thick restarts and stop
+ * rule, and leaves the batch when it stops, fails or reaches its k_max.  Each job's stream is
+ * synchronised on entry and on return (see svt_batch_options.concurrent for where the work runs).
+ * Outputs: results[i] as
+ * svt_solve's (ms = time from the batch's start to the end of the iteration in which job i left
+ * it), status[i] the job's own status.  Returns SVT_OK when every job met the stopping rule, else
+ * the first failing job's status (SVT_ERR_NOT_CONVERGED for k_max); SVT_ERR_ARG on a bad batch.
+ * svt_get_factors and the other per-context calls work on each job afterwards.
+ */
+svt_status svt_batch_solve(svt_ctx* const* jobs, int n, const double* tau, const double* delta, double eps,
+                           int max_rank, const svt_batch_options* opt, svt_result* results, svt_status* status);
 
 /*
  * Continuation in full: svt_configure(ctx, taus[0], delta, eps, max_rank, -1) (the kick of eq. (5.3)

@@ -294,6 +294,34 @@ class Solver:
                 for i, c in enumerate(_abi.PROF_CLASSES)}
 
 
+def batch_solve(solvers, tau=None, delta=None, eps: float = 1e-4, max_rank: int = 27, autotune: bool = False,
+                spmm_grid: int = 0, update_grid: int = 0, concurrent: bool = True):
+    """svt_batch_solve: Algorithm 1 for the problems of `solvers` (1 to 32 Solver objects of one
+    precision) at once, in lockstep, with the sparse products and the fused updates of all jobs as
+    single launches over the job list.  tau / delta: per-job sequences or None (defaults).  Returns
+    (list of SolveResult, list of per-job status codes); raises SVTError on a bad batch."""
+    L = library()
+    n = len(solvers)
+    ctxs = (ctypes.c_void_p * n)(*[s._ctx.value for s in solvers])
+    t = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
+    d = None if delta is None else np.ascontiguousarray(delta, dtype=np.float64)
+    opt = _abi.svt_batch_options()
+    L.svt_batch_default_options(ctypes.byref(opt))
+    opt.autotune = 1 if autotune else 0
+    opt.spmm_grid = spmm_grid
+    opt.update_grid = update_grid
+    opt.concurrent = 1 if concurrent else 0
+    res = (svt_result * n)()
+    st = np.zeros(n, dtype=np.int32)
+    rc = L.svt_batch_solve(ctypes.cast(ctxs, ctypes.c_void_p), n, None if t is None else t.ctypes.data,
+                           None if d is None else d.ctypes.data, eps, max_rank, ctypes.byref(opt),
+                           ctypes.cast(res, ctypes.c_void_p), st.ctypes.data)
+    if rc == _abi.SVT_ERR_ARG:
+        _check(rc, "svt_batch_solve", solvers[0]._ctx if n else None)
+    out = [SolveResult({f: getattr(r, f) for f, _ in svt_result._fields_}) for r in res]
+    return out, st.tolist()
+
+
 def sample_omega(m: int, n: int, nnz: int, seed: int, rows_out, cols_out, stream=None) -> None:
     """Device random-keys sampler of Omega into int32 device tensors rows_out/cols_out."""
     L = library()

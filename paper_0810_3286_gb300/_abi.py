@@ -97,6 +97,15 @@ class svt_result(ctypes.Structure):
     ]
 
 
+class svt_batch_options(ctypes.Structure):
+    _fields_ = [
+        ("spmm_grid", ctypes.c_int),
+        ("update_grid", ctypes.c_int),
+        ("autotune", ctypes.c_int),
+        ("concurrent", ctypes.c_int),
+    ]
+
+
 _vp = ctypes.c_void_p
 # svt_options.device_alloc / device_free
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -206,6 +215,9 @@ PROTOTYPES = {
     "svt_get_counters": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int]),
     "svt_set_barrier_spins": (ctypes.c_int, [_ctxp, ctypes.c_int]),
     "svt_set_tau": (ctypes.c_int, [_ctxp, ctypes.c_double]),
+    "svt_batch_default_options": (None, [ctypes.POINTER(svt_batch_options)]),
+    "svt_batch_solve": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(svt_batch_options), _vp, _vp]),
     "svt_selftest_math": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp]),
     "svt_solve_continuation": (ctypes.c_int, [_ctxp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                               ctypes.c_int, _vp, ctypes.POINTER(svt_result)]),

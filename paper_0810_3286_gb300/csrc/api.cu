@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -207,6 +208,15 @@ static void dev_free(svt_ctx* c, void* p) {
   if (!p) return;
   if (c->opt.device_free) c->opt.device_free(p, c->opt.alloc_user);
   else cudaFree(p);
+}
+
+// Frees one allocation that dalloc recorded in the context (so that svt_destroy does not free it
+// again).
+static void dfree(svt_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocations.begin(), c->allocations.end(), p);
+  if (it != c->allocations.end()) c->allocations.erase(it);
+  dev_free(c, p);
 }
 
 static svt_status dalloc(svt_ctx* c, void** p, size_t bytes) {
@@ -508,11 +518,16 @@ static svt_status orthonormalize(svt_ctx* c, double* P, const double* Q, long lo
 // an explicit restart from V_0 would build (its next block lies in the span of V_J), for two
 // sparse products and three orthonormalisations less.  Jprev: block steps of the previous cycle
 // (its basis, projected vectors and residual block V_Jprev); the cycle itself may use another J.
-static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk, bool copy_out = true) {
+//
+// The cycle is issued in pieces (cycle_begin, then per block step the sparse product Y V_j,
+// cycle_orth_left, the product Y^T U_j, cycle_orth_right, and cycle_end) so that the batched engine
+// can interleave the pieces of several jobs and run the sparse products of all of them as one
+// launch.
+static svt_status cycle_begin(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk, int* j0_out) {
   const int m = (int)c->m, n = (int)c->n;
-  const int K = J * b;
   const long long su = (long long)m * b, sv = (long long)n * b;
   int j0 = 0;
+  (void)J;
   if (!thick) {
     CU(c, cudaMemsetAsync(c->T, 0, sizeof(double) * kKMax * kKMax, c->st));
     TRY(orthonormalize(c, c->Vb, nullptr, 0, 0, n, b, nullptr, nullptr, c->Vsh));
@@ -537,27 +552,69 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, i
     TRY(launched(c, launch_set_diagonal(c->T, kKMax, c->theta, nk * b, c->st)));
     j0 = nk;
   }
-  int l = 0;
-  for (int j = j0; j < J; ++j) {
-    double* Uj = c->Ub + j * su;
-    double* Vj = c->Vb + j * sv;
-    l += prof_launch_f(c, SVT_PROF_SPMM, spmm_bytes(c, m, n, b), 2.0 * c->nnz * b, [&] {
-      return c->bf16_active
-                 ? launch_spmm(2, c->row_ptr, c->col_idx, c->Yb[c->ycur], Vj, c->Vsh, Uj, m, b, c->st, c->nnz)
-                 : launch_spmm(c->prec, c->row_ptr, c->col_idx, ycur_csr(c), Vj, c->Vsh, Uj, m, b, c->st, c->nnz);
-    });
-    TRY(launched(c, l)); l = 0;
-    TRY(orthonormalize(c, Uj, c->Ub, su, j, m, b, c->T + j * b, c->T + (long long)j * b * kKMax + j * b, c->Ush));
-    double* Vn = c->Vb + (j + 1) * sv;
-    l += prof_launch_f(c, SVT_PROF_SPMM_T, spmm_bytes(c, n, m, b), 2.0 * c->nnz * b, [&] {
-      return c->bf16_active
-                 ? launch_spmm(2, c->col_ptr, c->row_idx, c->Ybc[c->ycur], Uj, c->Ush, Vn, n, b, c->st, c->nnz)
-                 : launch_spmm(c->prec, c->col_ptr, c->row_idx, ycur_csc(c), Uj, c->Ush, Vn, n, b, c->st, c->nnz);
-    });
-    TRY(launched(c, l)); l = 0;
-    // the float32 copy of the last block V_J is kept for a thick restart
-    TRY(orthonormalize(c, Vn, c->Vb, sv, j + 1, n, b, nullptr, j == J - 1 ? c->S : nullptr, c->Vsh));
+  *j0_out = j0;
+  return SVT_OK;
+}
+
+// Launch precision of the sparse products: 0 float64, 1 float32, 2 bfloat16 values.
+static int spmm_precision(const svt_ctx* c) { return c->bf16_active ? 2 : (c->prec == SVT_FP64 ? 0 : 1); }
+
+// Operands of the sparse product of block step j: U_j = Y V_j (left) or V_{j+1} = Y^T U_j (right,
+// column-major copy of the values).
+static SpmmJob cycle_spmm_job(svt_ctx* c, int b, int j, bool left) {
+  const long long su = (long long)c->m * b, sv = (long long)c->n * b;
+  SpmmJob J{};
+  if (left) {
+    J.ptr = c->row_ptr;
+    J.idx = c->col_idx;
+    J.val = c->bf16_active ? static_cast<const void*>(c->Yb[c->ycur]) : ycur_csr(c);
+    J.X = c->Vb + j * sv;
+    J.Xf = c->Vsh;
+    J.Out = c->Ub + j * su;
+    J.n_out = (int)c->m;
+  } else {
+    J.ptr = c->col_ptr;
+    J.idx = c->row_idx;
+    J.val = c->bf16_active ? static_cast<const void*>(c->Ybc[c->ycur]) : ycur_csc(c);
+    J.X = c->Ub + j * su;
+    J.Xf = c->Ush;
+    J.Out = c->Vb + (j + 1) * sv;
+    J.n_out = (int)c->n;
   }
+  J.b = b;
+  J.nnz = c->nnz;
+  J.wpr = 0;
+  return J;
+}
+
+static svt_status cycle_spmm(svt_ctx* c, int b, int j, bool left) {
+  const SpmmJob J = cycle_spmm_job(c, b, j, left);
+  const int n_in = left ? (int)c->n : (int)c->m;
+  const int l = prof_launch_f(c, left ? SVT_PROF_SPMM : SVT_PROF_SPMM_T, spmm_bytes(c, J.n_out, n_in, b),
+                              2.0 * c->nnz * b, [&] {
+    return launch_spmm(spmm_precision(c), J.ptr, J.idx, J.val, J.X, J.Xf, J.Out, J.n_out, b, c->st, c->nnz);
+  });
+  return launched(c, l);
+}
+
+// U_j against U_0 .. U_{j-1}; its coefficients go to column block j of T.
+static svt_status cycle_orth_left(svt_ctx* c, int b, int j) {
+  const long long su = (long long)c->m * b;
+  return orthonormalize(c, c->Ub + j * su, c->Ub, su, j, (int)c->m, b, c->T + j * b,
+                        c->T + (long long)j * b * kKMax + j * b, c->Ush);
+}
+
+// V_{j+1} against V_0 .. V_j; the last block's R goes to S (the residual coupling) and its float32
+// copy is kept for a thick restart.
+static svt_status cycle_orth_right(svt_ctx* c, int b, int j, int J) {
+  const long long sv = (long long)c->n * b;
+  return orthonormalize(c, c->Vb + (j + 1) * sv, c->Vb, sv, j + 1, (int)c->n, b, nullptr,
+                        j == J - 1 ? c->S : nullptr, c->Vsh);
+}
+
+static svt_status cycle_end(svt_ctx* c, int b, int J, int nk, bool copy_out) {
+  const int K = J * b;
+  int l = 0;
   // S is written with leading dimension kKMax; the projected SVD reads it as b x b with leading
   // dimension b, so compact it first.
   CU(c, cudaMemcpy2DAsync(c->Rkeep, b * sizeof(double), c->S, kKMax * sizeof(double), b * sizeof(double), b,
@@ -584,6 +641,18 @@ static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, i
   CU(c, cudaMemcpyAsync(c->h_pin + kKMax, c->res, sizeof(double) * K, cudaMemcpyDeviceToHost, c->st));
   CU(c, cudaMemcpyAsync(c->h_pin + 3 * kKMax + 1, c->dcount + 3, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   return SVT_OK;
+}
+
+static svt_status issue_cycle(svt_ctx* c, int b, int J, bool thick, int Jprev, int nk, bool copy_out = true) {
+  int j0 = 0;
+  TRY(cycle_begin(c, b, J, thick, Jprev, nk, &j0));
+  for (int j = j0; j < J; ++j) {
+    TRY(cycle_spmm(c, b, j, true));
+    TRY(cycle_orth_left(c, b, j));
+    TRY(cycle_spmm(c, b, j, false));
+    TRY(cycle_orth_right(c, b, j, J));
+  }
+  return cycle_end(c, b, J, nk, copy_out);
 }
 
 // Captures issue_cycle for this (b, J, Y buffer, correction mode, restart kind) once and replays it
@@ -698,107 +767,138 @@ static svt_status keep_ritz(svt_ctx* c, int b, int J, int cols) {
 // converged values (host), *s_out the final s, *K_out/J_out/b_out the last cycle's shape.
 // strict: the first s_init triplets must all meet the residual tolerance and s never grows (used
 // for ||P_Omega M||_2, where the value itself matters).
-static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<double>& theta_out, int* s_out,
-                              int* passes_out, int* b_out, int* J_out, bool strict = false) {
-  const int kmin = (int)std::min(c->m, c->n);
-  // float32 values and products carry ~1e-6 of sigma_1 of rounding into the Lanczos relation
-  // (length-~100 float32 sums), so the float32 paths ask for ten times that; the float64 path asks
-  // for 1e-8: its iterates then agree with the float64 oracle to ~1e-8 (the bound is 1e-5), and
-  // tighter tolerances stall on some 30000 x 30000 shrinks
-  const double tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-8 : 1e-5);
-  int s = std::min(s_init, kmin);
-  int passes = 1;
-  int b = 0, J = 0, nk = 1;
-  cycle_shape(c, s, &b, &J, &nk);
-  c->last_cycles = 0;
-  c->last_spmm = 0;
-  int warm = std::min(c->warm_cols, b);
-  TRY(set_start_block(c, b, warm));
-  const int max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
+// One rank-adaptive partial SVD in progress: the state partial_svd carries from one Lanczos cycle
+// to the next (the batched engine keeps one per job).
+struct ShrinkRun {
+  double tau = 0.0, tol = 0.0;
+  int kmin = 0, s = 0, passes = 1, b = 0, J = 0, nk = 1, max_cycles = 40;
   bool thick = false;   // the next cycle is a thick restart of the previous one
   int Jprev = 0;        // block steps of the previous cycle
   // cycles of the current pass of the rank policy: each pass is a partial SVD of its own (Sec. 5.1.1
   // asks the partial SVD for s_k triplets, then for s_k + l, ...), with its own cycle budget and
   // stagnation clock
   int cyc = 0;
-  for (;; ++cyc) {
-    const double *th, *rs;
-    TRY(lanczos_cycle(c, b, J, thick, Jprev, nk, &th, &rs));
-    if (!std::isfinite(th[0]) || !std::isfinite(rs[0]))
-      return fail(c, SVT_ERR_NUMERIC, "non-finite Ritz value or residual estimate");
-    // stagnation: a cluster of Ritz values that the working precision cannot separate further
-    // keeps its residuals above tol; after 10 cycles of one shrink the tolerance is relaxed 30x,
-    // after 25 cycles 300x (recorded in the relaxed_shrinks counter)
-    const double tol_c = cyc >= 25 ? 300.0 * tol : (cyc >= 10 ? 30.0 * tol : tol);
-    thick = false;
-    Jprev = J;
-    const int K = J * b;
-    const int s_eff = std::min(s, K);
-    // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
-    // theta_s > tau already proves sigma_s > tau: the rank policy grows s without waiting for
-    // convergence.  Otherwise every Ritz triplet above tau must be converged to `tol`, and the
-    // first Ritz value at or below tau must be resolved (residual <= 1e-3 theta_1: the Krylov
-    // space has found the singular value it stands for; an unresolved Ritz value with a large
-    // residual bounds no particular singular value) and bounded away from tau
-    // (theta + residual <= tau).
-    const bool grow = !strict && th[s_eff - 1] > tau && s < kmin;
-    int conv = 0;
-    bool all_conv = !grow;
-    for (int i = 0; i < s_eff && all_conv; ++i) {
-      const bool above = strict || th[i] > tau;
-      const bool ok = rs[i] <= tol_c * th[0] || (!above && rs[i] <= 1e-3 * th[0] && th[i] + rs[i] <= tau);
-      if (!ok) all_conv = false;
-      else ++conv;
-      if (!above) break;
-    }
-    if (all_conv || grow) {
-      if (grow) {
-        if (s + c->opt.ell > kMaxRankCap + 1) {
-          theta_out.assign(th, th + s_eff);
-          *s_out = s;
-          return fail(c, SVT_ERR_RANK_LIMIT, "more than %d singular values exceed tau", kMaxRankCap);
-        }
-        s = std::min(s + c->opt.ell, kmin);
-        ++passes;
-        int nb = 0;
-        cycle_shape(c, s, &nb, &J, &nk);
-        TRY(keep_ritz(c, b, Jprev, std::min(b, nb)));
-        b = nb;
-        TRY(set_start_block(c, b, std::min(c->warm_cols, b)));
-        cyc = -1;
-        continue;
+  bool strict = false;
+};
+
+static svt_status shrink_start(svt_ctx* c, ShrinkRun& R, int s_init, double tau, bool strict) {
+  R.kmin = (int)std::min(c->m, c->n);
+  // float32 values and products carry ~1e-6 of sigma_1 of rounding into the Lanczos relation
+  // (length-~100 float32 sums), so the float32 paths ask for ten times that; the float64 path asks
+  // for 1e-8: its iterates then agree with the float64 oracle to ~1e-8 (the bound is 1e-5), and
+  // tighter tolerances stall on some 30000 x 30000 shrinks
+  R.tol = c->opt.lanczos_tol > 0 ? c->opt.lanczos_tol : (c->prec == SVT_FP64 ? 1e-8 : 1e-5);
+  R.tau = tau;
+  R.strict = strict;
+  R.s = std::min(s_init, R.kmin);
+  R.passes = 1;
+  cycle_shape(c, R.s, &R.b, &R.J, &R.nk);
+  c->last_cycles = 0;
+  c->last_spmm = 0;
+  TRY(set_start_block(c, R.b, std::min(c->warm_cols, R.b)));
+  R.max_cycles = c->opt.max_cycles > 0 ? c->opt.max_cycles : 40;
+  R.thick = false;
+  R.Jprev = 0;
+  R.cyc = 0;
+  return SVT_OK;
+}
+
+// Applies the rank policy and the convergence test to the Ritz values th and residual estimates
+// rs of the cycle just run.  *done: the partial SVD is finished (theta_out, *s_out, ... set);
+// otherwise R holds the shape of the next cycle (its start block is issued).
+static svt_status shrink_advance(svt_ctx* c, ShrinkRun& R, const double* th, const double* rs, bool* done,
+                                 std::vector<double>& theta_out, int* s_out, int* passes_out, int* b_out, int* J_out) {
+  *done = false;
+  if (!std::isfinite(th[0]) || !std::isfinite(rs[0]))
+    return fail(c, SVT_ERR_NUMERIC, "non-finite Ritz value or residual estimate");
+  // stagnation: a cluster of Ritz values that the working precision cannot separate further
+  // keeps its residuals above tol; after 10 cycles of one shrink the tolerance is relaxed 30x,
+  // after 25 cycles 300x (recorded in the relaxed_shrinks counter)
+  const double tol_c = R.cyc >= 25 ? 300.0 * R.tol : (R.cyc >= 10 ? 30.0 * R.tol : R.tol);
+  R.thick = false;
+  R.Jprev = R.J;
+  const int b = R.b;
+  const int K = R.J * b;
+  const int s_eff = std::min(R.s, K);
+  // Ritz values are lower bounds of the singular values (interlacing of U^T Y V), so
+  // theta_s > tau already proves sigma_s > tau: the rank policy grows s without waiting for
+  // convergence.  Otherwise every Ritz triplet above tau must be converged to `tol`, and the
+  // first Ritz value at or below tau must be resolved (residual <= 1e-3 theta_1: the Krylov
+  // space has found the singular value it stands for; an unresolved Ritz value with a large
+  // residual bounds no particular singular value) and bounded away from tau
+  // (theta + residual <= tau).
+  const double tau = R.tau;
+  const bool grow = !R.strict && th[s_eff - 1] > tau && R.s < R.kmin;
+  int conv = 0;
+  bool all_conv = !grow;
+  for (int i = 0; i < s_eff && all_conv; ++i) {
+    const bool above = R.strict || th[i] > tau;
+    const bool ok = rs[i] <= tol_c * th[0] || (!above && rs[i] <= 1e-3 * th[0] && th[i] + rs[i] <= tau);
+    if (!ok) all_conv = false;
+    else ++conv;
+    if (!above) break;
+  }
+  if (all_conv || grow) {
+    if (grow) {
+      if (R.s + c->opt.ell > kMaxRankCap + 1) {
+        theta_out.assign(th, th + s_eff);
+        *s_out = R.s;
+        return fail(c, SVT_ERR_RANK_LIMIT, "more than %d singular values exceed tau", kMaxRankCap);
       }
-      theta_out.assign(th, th + s_eff);
-      *s_out = s_eff;
-      *passes_out = passes;
-      if (cyc >= 10) c->relaxed_shrinks += 1;
-      *b_out = b;
-      *J_out = J;
+      R.s = std::min(R.s + c->opt.ell, R.kmin);
+      ++R.passes;
+      int nb = 0;
+      cycle_shape(c, R.s, &nb, &R.J, &R.nk);
+      TRY(keep_ritz(c, b, R.Jprev, std::min(b, nb)));
+      R.b = nb;
+      TRY(set_start_block(c, R.b, std::min(c->warm_cols, R.b)));
+      R.cyc = 0;
       return SVT_OK;
     }
-    if (cyc + 1 >= max_cycles)
-      return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
-                  max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
-    // not converged, same block: continue from the leading Ritz pairs (nk blocks) and the residual
-    // block, extending the space by restart_steps - nk blocks
-    int Jr = std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : J, kKMax / b);
-    Jr = std::max(Jr, std::min(nk + 1, kKMax / b));
-    if (Jr >= nk + 1) {
-      thick = true;
-      J = Jr;
-    } else {
-      TRY(keep_ritz(c, b, J, b));
-      TRY(set_start_block(c, b, b));
-    }
+    theta_out.assign(th, th + s_eff);
+    *s_out = s_eff;
+    *passes_out = R.passes;
+    if (R.cyc >= 10) c->relaxed_shrinks += 1;
+    *b_out = b;
+    *J_out = R.J;
+    *done = true;
+    return SVT_OK;
+  }
+  if (R.cyc + 1 >= R.max_cycles)
+    return fail(c, SVT_ERR_NUMERIC, "Lanczos did not converge in %d cycles (converged %d of %d, res %.3e)",
+                R.max_cycles, conv, s_eff, rs[std::min(conv, s_eff - 1)] / th[0]);
+  // not converged, same block: continue from the leading Ritz pairs (nk blocks) and the residual
+  // block, extending the space by restart_steps - nk blocks
+  int Jr = std::min(c->opt.restart_steps > 0 ? c->opt.restart_steps : R.J, kKMax / b);
+  Jr = std::max(Jr, std::min(R.nk + 1, kKMax / b));
+  if (Jr >= R.nk + 1) {
+    R.thick = true;
+    R.J = Jr;
+  } else {
+    TRY(keep_ritz(c, b, R.J, b));
+    TRY(set_start_block(c, b, b));
+  }
+  ++R.cyc;
+  return SVT_OK;
+}
+
+static svt_status partial_svd(svt_ctx* c, int s_init, double tau, std::vector<double>& theta_out, int* s_out,
+                              int* passes_out, int* b_out, int* J_out, bool strict = false) {
+  ShrinkRun R;
+  TRY(shrink_start(c, R, s_init, tau, strict));
+  for (;;) {
+    const double *th, *rs;
+    TRY(lanczos_cycle(c, R.b, R.J, R.thick, R.Jprev, R.nk, &th, &rs));
+    bool done = false;
+    TRY(shrink_advance(c, R, th, rs, &done, theta_out, s_out, passes_out, b_out, J_out));
+    if (done) return SVT_OK;
   }
 }
 
 // X = D_tau(Y): factors of the triplets with sigma > tau from the last cycle.
-static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out) {
-  NvtxRange nv("svt: shrink D_tau (rank-adaptive partial SVD, Ritz vectors)");
-  std::vector<double> th;
-  int s = 0, passes = 0, b = 0, J = 0;
-  TRY(partial_svd(c, s_init, tau, th, &s, &passes, &b, &J));
+// The factors of D_tau(Y) from the converged Ritz triplets th of the last cycle (shape b, J).
+static svt_status shrink_finish(svt_ctx* c, double tau, const std::vector<double>& th, int s, int passes, int b,
+                                int J, int* r_out) {
   int r = 0;
   while (r < (int)th.size() && th[r] > tau) ++r;
   if (r > c->max_rank) return fail(c, SVT_ERR_RANK_LIMIT, "rank %d exceeds max_rank %d", r, c->max_rank);
@@ -831,6 +931,14 @@ static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out)
   c->r = r;
   *r_out = r;
   return SVT_OK;
+}
+
+static svt_status shrink_current(svt_ctx* c, double tau, int s_init, int* r_out) {
+  NvtxRange nv("svt: shrink D_tau (rank-adaptive partial SVD, Ritz vectors)");
+  std::vector<double> th;
+  int s = 0, passes = 0, b = 0, J = 0;
+  TRY(partial_svd(c, s_init, tau, th, &s, &passes, &b, &J));
+  return shrink_finish(c, tau, th, s, passes, b, J, r_out);
 }
 
 // D_tau(Y) by a randomized range finder (Sec. 6, the first of the two alternatives the paper names):
@@ -1704,6 +1812,395 @@ extern "C" svt_status svt_set_tau(svt_ctx* c, double tau) {
   if (!c->configured) return fail(c, SVT_ERR_ARG, "svt_configure (or svt_solve) must come first");
   c->tau = tau;
   c->k = 0;
+  return SVT_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched engine: Algorithm 1 for several independent completion problems at once, in lockstep.
+// Every SVT iteration of the batch runs the shrinks of all unfinished jobs together, one Lanczos
+// cycle of every still-shrinking job at a time; inside a cycle the sparse products of all jobs at
+// the same block step are one persistent launch over the job list (launch_spmm_jobs), and the
+// fused updates of all jobs are one launch (launch_sddmm_update_jobs).  Orthonormalisations,
+// projected SVDs and Ritz vectors stay per job.  Each job's decisions (rank policy, convergence,
+// thick restarts, stop rule) are those of its solo run; with the fixed tile rule its sparse
+// products are computed exactly as solo, so every iterate equals the solo iterate (the residual
+// sums differ in grouping only).  One host synchronisation per lockstep cycle and one per
+// iteration serve the whole batch.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+// Warps per segment chosen by the tuner, per (precision, block, direction, mean segment length
+// class), for the whole process.
+struct TuneKey {
+  int prec, b, left, len_class;
+  bool operator==(const TuneKey& o) const {
+    return prec == o.prec && b == o.b && left == o.left && len_class == o.len_class;
+  }
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, int>> g_tune;
+
+int len_class(long long nnz, int n_out) {
+  const double mean = n_out > 0 ? (double)nnz / n_out : 0.0;
+  int k = 0;
+  while (k < 30 && (double)(1LL << (k + 1)) <= mean) ++k;
+  return k;
+}
+
+}  // namespace
+
+// Times the candidate tile shapes (warps per segment 1, 2, 4, 8) of one product on the batch
+// stream and returns the fastest.  Runs real products (into the job's own output block, which the
+// batched launch overwrites), three timed launches per candidate after one untimed.
+static int tune_spmm(svt_ctx* c, const SpmmJob& J0, int prec, cudaStream_t st) {
+  cudaEvent_t a = nullptr, z = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&z) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    (void)cudaGetLastError();
+    return 0;
+  }
+  int best = 0;
+  float best_ms = 0.f;
+  for (int w = 1; w <= 8; w <<= 1) {
+    SpmmJob J = J0;
+    J.wpr = w;
+    launch_spmm_jobs(prec, &J, 1, 0, st);
+    cudaEventRecord(a, st);
+    for (int rep = 0; rep < 3; ++rep) launch_spmm_jobs(prec, &J, 1, 0, st);
+    cudaEventRecord(z, st);
+    if (cudaEventSynchronize(z) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, z);
+    if (best == 0 || ms < best_ms) {
+      best = w;
+      best_ms = ms;
+    }
+    c->launches += 4;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(z);
+  (void)cudaGetLastError();
+  return best;
+}
+
+static int tuned_wpr(svt_ctx* c, const SpmmJob& J, int prec, bool left, cudaStream_t st) {
+  const TuneKey key{prec, J.b, left ? 1 : 0, len_class(J.nnz, J.n_out)};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& e : g_tune)
+      if (e.first == key) return e.second;
+  }
+  const int w = tune_spmm(c, J, prec, st);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune.push_back({key, w});
+  return w;
+}
+
+extern "C" void svt_batch_default_options(svt_batch_options* opt) {
+  if (!opt) return;
+  opt->spmm_grid = 0;
+  opt->update_grid = 0;
+  opt->autotune = 0;
+  opt->concurrent = 1;
+}
+
+// Restores every job's stream and cooperative grid, and releases the batch's own stream and
+// events, when the batch returns.
+struct BatchStreams {
+  std::vector<svt_ctx*> jobs;
+  std::vector<cudaStream_t> saved;
+  std::vector<int> saved_grid;
+  std::vector<cudaEvent_t> ev;
+  cudaStream_t own = nullptr;
+  ~BatchStreams() {
+    if (own) cudaStreamSynchronize(own);
+    for (size_t i = 0; i < jobs.size(); ++i) {
+      cudaStreamSynchronize(jobs[i]->st);
+      jobs[i]->st = saved[i];
+      jobs[i]->coop_grid = saved_grid[i];
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (own) cudaStreamDestroy(own);
+  }
+};
+
+extern "C" svt_status svt_batch_solve(svt_ctx* const* jobs, int n, const double* tau, const double* delta,
+                                      double eps, int max_rank, const svt_batch_options* opt, svt_result* results,
+                                      svt_status* status) {
+  if (!jobs || n < 1 || n > kBatchMaxJobs || !results || !status) return SVT_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!jobs[i]) return SVT_ERR_ARG;
+    for (int k = 0; k < i; ++k)
+      if (jobs[k] == jobs[i]) return fail(jobs[i], SVT_ERR_ARG, "a context appears twice in the batch");
+  }
+  svt_batch_options bo;
+  svt_batch_default_options(&bo);
+  if (opt) bo = *opt;
+  svt_ctx* c0 = jobs[0];
+  for (int i = 0; i < n; ++i) {
+    svt_ctx* c = jobs[i];
+    if (c->prec != c0->prec || c->bf16_mode)
+      return fail(c, SVT_ERR_ARG, "a batch needs one value precision (FP64 or FP32) for all jobs");
+    if (c->ds_E > 0.0 || c->noise_sigma > 0.0 || c->opt.shrink_engine != SVT_SHRINK_LANCZOS)
+      return fail(c, SVT_ERR_ARG, "batched jobs run the plain iteration with the Lanczos shrink");
+    if (c->coop_grid <= 0) return fail(c, SVT_ERR_ARG, "batched jobs need the cooperative orthonormalisation");
+  }
+  NvtxRange nv("svt_batch_solve");
+  // earlier work of every job is finished first
+  for (int i = 0; i < n; ++i) {
+    CU(jobs[i], cudaStreamSynchronize(jobs[i]->user_st));
+    CU(jobs[i], cudaStreamSynchronize(jobs[i]->st));
+  }
+  BatchStreams guard;
+  for (int i = 0; i < n; ++i) {
+    guard.jobs.push_back(jobs[i]);
+    guard.saved.push_back(jobs[i]->st);
+    guard.saved_grid.push_back(jobs[i]->coop_grid);
+  }
+  // concurrent: the batched launches run on a stream of the batch's own, every job's own work on
+  // its library stream (events order the two), and each job's cooperative orthonormalisation gets
+  // max(16, 2 SMs / n) CTAs so that the jobs' kernels overlap on the GPU; otherwise everything runs
+  // on the first job's stream with the solo launch shapes (every iterate equals the solo one)
+  const bool conc = bo.concurrent != 0 && n > 1;
+  cudaStream_t bst = c0->st;
+  if (conc) {
+    CU(c0, cudaStreamCreateWithFlags(&guard.own, cudaStreamNonBlocking));
+    bst = guard.own;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int i = 0; i < n; ++i) {
+      jobs[i]->coop_grid = std::min(jobs[i]->coop_grid, std::max(16, 2 * sms / n));
+      cudaEvent_t e = nullptr;
+      CU(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      guard.ev.push_back(e);
+    }
+    cudaEvent_t e = nullptr;
+    CU(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    guard.ev.push_back(e);   // the batch stream's event, last
+  } else {
+    for (int i = 0; i < n; ++i) jobs[i]->st = bst;
+  }
+  // the batch stream waits for the listed jobs' streams; then the jobs' streams wait for it
+  auto batch_after_jobs = [&](const std::vector<int>& L) -> svt_status {
+    if (!conc) return SVT_OK;
+    for (int i : L) {
+      CU(c0, cudaEventRecord(guard.ev[i], jobs[i]->st));
+      CU(c0, cudaStreamWaitEvent(bst, guard.ev[i], 0));
+    }
+    return SVT_OK;
+  };
+  auto jobs_after_batch = [&](const std::vector<int>& L) -> svt_status {
+    if (!conc) return SVT_OK;
+    CU(c0, cudaEventRecord(guard.ev[n], bst));
+    for (int i : L) CU(c0, cudaStreamWaitEvent(jobs[i]->st, guard.ev[n], 0));
+    return SVT_OK;
+  };
+  const int prec = c0->prec == SVT_FP64 ? 0 : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(c0, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(c0, SVT_ERR_CUDA, "cudaEventCreate failed");
+  }
+  struct EvGuard {
+    cudaEvent_t a, b;
+    ~EvGuard() { cudaEventDestroy(a); cudaEventDestroy(b); }
+  } evg{e0, e1};
+  CU(c0, cudaEventRecord(e0, bst));
+  if (conc)
+    for (int i = 0; i < n; ++i) CU(c0, cudaStreamWaitEvent(jobs[i]->st, e0, 0));
+  std::vector<int> alive;
+  std::vector<int64_t> spmm0(n), cyc0(n);
+  for (int i = 0; i < n; ++i) {
+    svt_ctx* c = jobs[i];
+    results[i] = svt_result{};
+    spmm0[i] = c->total_spmm;
+    cyc0[i] = c->total_cycles;
+    status[i] = svt_configure(c, tau ? tau[i] : 0.0, delta ? delta[i] : 0.0, eps, max_rank, -1);
+    if (status[i] == SVT_OK) alive.push_back(i);
+  }
+  // tile partials of the batched update: one per 64 rows of every job
+  std::vector<int> mrows(n);
+  for (int i = 0; i < n; ++i) mrows[i] = (int)jobs[i]->m;
+  const long long cap = upd_jobs_tiles(mrows.data(), n);
+  double* partial = nullptr;
+  TRY(dalloc_t(c0, &partial, (size_t)cap + 1));
+  struct PartialGuard {
+    svt_ctx* c;
+    double* p;
+    ~PartialGuard() { dfree(c, p); }
+  } pg{c0, partial};
+  unsigned int* berr = reinterpret_cast<unsigned int*>(partial + cap);
+  CU(c0, cudaMemsetAsync(berr, 0, sizeof(unsigned int), bst));
+  int64_t batch_launches = 0;
+  auto drop = [&](std::vector<int>& v, int i) { v.erase(std::find(v.begin(), v.end(), i)); };
+
+  while (!alive.empty()) {
+    // ---- shrink of every unfinished job: lockstep Lanczos cycles ----
+    std::vector<ShrinkRun> R(n);
+    std::vector<std::vector<double>> th(n);
+    std::vector<int> sh_s(n), sh_passes(n), sh_b(n), sh_J(n), j0(n);
+    std::vector<int> shrinking;
+    for (int i : std::vector<int>(alive)) {
+      svt_ctx* c = jobs[i];
+      const int kmin = (int)std::min(c->m, c->n);
+      const svt_status st = shrink_start(c, R[i], std::min(c->r + 1, kmin), c->tau, false);
+      if (st != SVT_OK) {
+        status[i] = st;
+        drop(alive, i);
+      } else {
+        shrinking.push_back(i);
+      }
+    }
+    while (!shrinking.empty()) {
+      int Jmax = 0;
+      for (int i : std::vector<int>(shrinking)) {
+        const svt_status st = cycle_begin(jobs[i], R[i].b, R[i].J, R[i].thick, R[i].Jprev, R[i].nk, &j0[i]);
+        if (st != SVT_OK) {
+          status[i] = st;
+          drop(shrinking, i);
+          drop(alive, i);
+          continue;
+        }
+        Jmax = std::max(Jmax, R[i].J);
+      }
+      for (int j = 0; j < Jmax; ++j) {
+        std::vector<int> L;
+        for (int i : shrinking)
+          if (j >= j0[i] && j < R[i].J) L.push_back(i);
+        if (L.empty()) continue;
+        for (int side = 0; side < 2; ++side) {
+          const bool left = side == 0;
+          std::vector<SpmmJob> sj;
+          for (int i : L) {
+            SpmmJob J = cycle_spmm_job(jobs[i], R[i].b, j, left);
+            if (bo.autotune) J.wpr = tuned_wpr(jobs[i], J, prec, left, bst);
+            sj.push_back(J);
+          }
+          TRY(batch_after_jobs(L));
+          if (launch_spmm_jobs(prec, sj.data(), (int)sj.size(), bo.spmm_grid, bst) != 1)
+            return fail(c0, SVT_ERR_CUDA, "batched sparse product launch failed: %s",
+                        cudaGetErrorString(cudaGetLastError()));
+          ++batch_launches;
+          TRY(jobs_after_batch(L));
+          for (int i : L) {
+            const int nspmm = 1;
+            jobs[i]->last_spmm += nspmm;
+            jobs[i]->total_spmm += nspmm;
+            const svt_status st = left ? cycle_orth_left(jobs[i], R[i].b, j)
+                                       : cycle_orth_right(jobs[i], R[i].b, j, R[i].J);
+            if (st != SVT_OK) return st;   // a launch failed: the batch stream is unusable
+          }
+        }
+      }
+      for (int i : shrinking) {
+        svt_ctx* c = jobs[i];
+        TRY(cycle_end(c, R[i].b, R[i].J, R[i].nk, true));
+        c->last_cycles += 1;
+        c->total_cycles += 1;
+        unsigned int* herr = reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1);
+        CU(c, cudaMemcpyAsync(herr, c->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+      }
+      if (conc) {
+        for (int i : shrinking) CU(jobs[i], cudaStreamSynchronize(jobs[i]->st));
+      } else {
+        CU(c0, cudaStreamSynchronize(bst));
+      }
+      for (int i : std::vector<int>(shrinking)) {
+        svt_ctx* c = jobs[i];
+        prof_harvest(c);
+        svt_status st = check_err_word(c, *reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1));
+        if (st == SVT_OK) {
+          double defect = 0.0;
+          std::memcpy(&defect, c->h_pin + 3 * kKMax + 1, sizeof defect);
+          if (defect > 1e-6) c->two_corrections = true;
+          bool done = false;
+          st = shrink_advance(c, R[i], c->h_pin, c->h_pin + kKMax, &done, th[i], &sh_s[i], &sh_passes[i], &sh_b[i],
+                              &sh_J[i]);
+          if (st == SVT_OK && !done) continue;
+          if (st == SVT_OK) {
+            int r = 0;
+            st = shrink_finish(c, c->tau, th[i], sh_s[i], sh_passes[i], sh_b[i], sh_J[i], &r);
+          }
+        }
+        drop(shrinking, i);
+        if (st != SVT_OK) {
+          status[i] = st;
+          drop(alive, i);
+        }
+      }
+    }
+    if (alive.empty()) break;
+    // ---- fused update of every unfinished job: one launch ----
+    std::vector<UpdJob> uj;
+    for (int i : alive) {
+      svt_ctx* c = jobs[i];
+      const int nxt = 1 - c->ycur;
+      UpdJob u{};
+      u.row_ptr = c->row_ptr;
+      u.col_idx = c->col_idx;
+      u.csr_to_csc = c->csr_to_csc;
+      u.M = c->Mv;
+      u.y_in = ycur_csr(c);
+      u.y_out = c->Ycsr[nxt];
+      u.y_out_csc = c->Ycsc[nxt];
+      if (prec == 0) {
+        u.Ut = c->Ut;
+        u.V = c->Vf;
+        u.ldf = c->r;
+      } else {
+        u.Ut = c->Utf;
+        u.V = c->Vff;
+        u.ldf = c->ldf;
+      }
+      u.r = c->r;
+      u.m = (int)c->m;
+      u.delta = c->delta;
+      u.res2 = c->dscal;
+      uj.push_back(u);
+    }
+    TRY(batch_after_jobs(alive));
+    if (launch_sddmm_update_jobs(prec, uj.data(), (int)uj.size(), partial, cap, berr, bo.update_grid, bst) != 2)
+      return fail(c0, SVT_ERR_CUDA, "batched update launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    batch_launches += 2;
+    for (int i : alive)
+      CU(jobs[i], cudaMemcpyAsync(jobs[i]->h_pin + 3 * kKMax, jobs[i]->dscal, sizeof(double), cudaMemcpyDeviceToHost,
+                                  bst));
+    CU(c0, cudaEventRecord(e1, bst));
+    CU(c0, cudaEventSynchronize(e1));
+    TRY(jobs_after_batch(alive));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    for (int i : std::vector<int>(alive)) {
+      svt_ctx* c = jobs[i];
+      const svt_status st = finish_step(c, c->r, c->h_pin[3 * kKMax], ms, nullptr);
+      svt_result& res = results[i];
+      res.iterations = c->k;
+      res.k0 = c->k0;
+      res.rank = c->r;
+      res.residual = std::sqrt(c->h_pin[3 * kKMax]) / c->normF;
+      res.norm2_M = c->norm2;
+      res.normF_M = c->normF;
+      res.ms = ms;
+      res.spmm_calls = c->total_spmm - spmm0[i];
+      res.lanczos_cycles = c->total_cycles - cyc0[i];
+      if (st == SVT_STOPPED) {
+        res.converged = 1;
+        status[i] = SVT_OK;
+        drop(alive, i);
+      } else if (st != SVT_OK) {
+        status[i] = st;
+        drop(alive, i);
+      } else if (c->k >= c->opt.k_max) {
+        status[i] = fail(c, SVT_ERR_NOT_CONVERGED, "k_max iterations reached");
+        drop(alive, i);
+      }
+    }
+  }
+  c0->launches += batch_launches;
+  for (int i = 0; i < n; ++i)
+    if (status[i] != SVT_OK) return status[i] == SVT_ERR_NOT_CONVERGED ? SVT_ERR_NOT_CONVERGED : status[i];
   return SVT_OK;
 }
 

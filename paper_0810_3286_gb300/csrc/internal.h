@@ -61,6 +61,36 @@ int launch_omega_compact(uint64_t seed, long long N, long long n_cols, const voi
 int launch_spmm(int precision, const int32_t* ptr, const int32_t* idx, const void* val, const double* X,
                 const float* Xf, double* Out, int n_out, int b, cudaStream_t st, long long nnz);
 
+// Batched engine: one launch runs the sparse products (or the fused updates) of up to
+// kBatchMaxJobs jobs of different shapes.  The job table travels as a kernel parameter.
+static constexpr int kBatchMaxJobs = 32;
+
+struct SpmmJob {                 // host description of one product Out = S X of a job list
+  const int32_t* ptr;            // segment pointers (n_out + 1)
+  const int32_t* idx;            // entry indices
+  const void* val;               // entry values (float64, float32 or bfloat16 by the launch precision)
+  const double* X;               // float64 block (precision 0)
+  const float* Xf;               // float32 copy of the block (precisions 1 and 2)
+  double* Out;                   // n_out x b
+  int n_out, b;
+  long long nnz;
+  int wpr;                       // warps per segment; 0: the rule of launch_spmm
+};
+struct SpmmJobDev {
+  const int32_t* ptr;
+  const int32_t* idx;
+  const void* val;
+  const void* X;
+  double* Out;
+  int n_out, b, G, WPR, tile0;
+};
+struct SpmmJobTable {
+  int n, tiles;
+  SpmmJobDev job[kBatchMaxJobs];
+};
+// grid: CTAs of the persistent launch (0: 16 per SM).  Returns launches issued (0 on bad input).
+int launch_spmm_jobs(int precision, const SpmmJob* jobs, int n, int grid, cudaStream_t st);
+
 // Gram of a tall block against a basis: G ((nq+1) b x b) = [Q_0 .. Q_{nq-1}, P]^T P, where the Q_i
 // are n x b blocks spaced `q_stride` doubles apart.  partial: gram_partial_doubles(...) doubles.
 long long gram_partial_doubles(int n, int nq, int b);
@@ -197,6 +227,45 @@ int launch_dual_kick(int precision, const void* B, double alpha, double E, void*
 int sddmm_partial_doubles();
 // The same fused kernel (float64 values, no column-major copy) on `blocks` CTAs of 256 threads,
 // one partial sum per CTA in `partial`, the fixed-order total in *res2 (device).
+// Fused update of a job list (plain form: no Dantzig multipliers, no bfloat16 copies).  Per job:
+// y_out = y_in + delta (M - x) in both orders and res2 = sum (M - x)^2, x = <Ut_i, V_j> on Omega.
+struct UpdJob {
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const int32_t* csr_to_csc;
+  const void* M;
+  const void* y_in;
+  void* y_out;
+  void* y_out_csc;
+  const void* Ut;                // factors: float64 (precision 0) or float32 rows padded to ldf
+  const void* V;
+  int r, ldf, m;
+  double delta;
+  double* res2;                  // device scalar
+};
+struct UpdJobDev {
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const int32_t* csr_to_csc;
+  const void* M;
+  const void* y_in;
+  void* y_out;
+  void* y_out_csc;
+  const void* Ut;
+  const void* V;
+  double* res2;
+  double delta;
+  int r, ldf, m, tile0;
+};
+struct UpdJobTable {
+  int n, tiles;
+  UpdJobDev job[kBatchMaxJobs];
+};
+// partial: one double per tile of 64 rows over all jobs (upd_jobs_partial_doubles bounds it).
+int launch_sddmm_update_jobs(int precision, const UpdJob* jobs, int n, double* partial, long long partial_cap,
+                             unsigned int* err, int grid, cudaStream_t st);
+long long upd_jobs_tiles(const int* m, int n);
+
 int launch_sddmm_update_grid(const int32_t* row_ptr, const int32_t* col_idx, const double* M, const double* y_in,
                              double* y_out, const double* Ut, const double* V, int r, int n_rows, double delta,
                              int blocks, double* partial, double* res2, cudaStream_t st);

@@ -91,7 +91,7 @@ def test_binding_struct_layouts_match_the_headers(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = [_abi.svt_options, _abi.svt_step_info, _abi.svt_result, _abi.svt_server_options, _abi.svt_job,
+    structs = [_abi.svt_options, _abi.svt_step_info, _abi.svt_result, _abi.svt_batch_options, _abi.svt_server_options, _abi.svt_job,
                _abi.svt_job_result, _abi.svt_server_stats]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "svt.h"', '#include "svt_serve.h"',
              'int main(void) {']
