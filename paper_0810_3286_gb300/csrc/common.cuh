@@ -20,6 +20,11 @@ __device__ __forceinline__ void svt_set_error(unsigned int* err, unsigned int bi
   if (err) atomicOr(err, bit);
 }
 
+// Fused multiply-add in the argument type (float: fmaf, double: fma), so that templated kernels
+// never promote a float32 accumulation to float64.
+__device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return fma(a, b, c); }
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -38,7 +38,7 @@ k_basis_combine(const double* __restrict__ B, long long b_stride, int nb, int b,
     for (int blk = 0; blk < nb; ++blk) {
       const double* brow = B + blk * b_stride + (long long)i * b;
       const double* wcol = sW + (blk * b) * s + c;
-      for (int d = 0; d < b; ++d) v += brow[d] * wcol[d * s];
+      for (int d = 0; d < b; ++d) v = fma(brow[d], wcol[d * s], v);
     }
     Out[(long long)i * ldo + c] = v;
     if (OutF) OutF[(long long)i * ldF + c] = (float)v;

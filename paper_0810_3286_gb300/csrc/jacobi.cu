@@ -21,10 +21,14 @@
 //     rotations themselves (the left vectors) are not accumulated.
 // Residual estimates of the Lanczos relation: res_k = || S x_k[last b rows] || with S the b x b
 // upper triangular factor of the last block (Y^T U_J = V T^T + V_{J+1} S E_J^T).
+#include <cooperative_groups.h>
+
 #include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace svt {
 
@@ -258,12 +262,27 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 //      tolerance of 1e-8 sigma_1 they are tested against).  The right vectors of the leading
 //      b triplets are then w = T^T g / ||g||^2 for the final columns g = theta x of G.
 // The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
+//
+// Launched as a thread-block cluster (launch_small_svd: 8 CTAs where the device allows it), the
+// dense float64 products are spread over the cluster: CTA 0 holds G / W, the column norms and the
+// order in its shared memory and runs phase A and the sweeps alone; E = W^T W - I (entries), W's
+// correction (rows), G = T W (columns), the norms of G, the right vectors (entries) and the
+// residual estimates (triplets) are shared by all CTAs through distributed shared memory, with a
+// cluster barrier between phases.  (Sweeps spread over the cluster, one warp per pair and a cluster
+// barrier per round, measured slower: ~12k cycles a round against ~10k in one CTA.)  With one CTA
+// the kernel is the single-CTA form.
 template <int JR>
 __global__ void __launch_bounds__(512)
 k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restrict__ S, int b, int nv,
              double* __restrict__ theta, double* __restrict__ Xl, double* __restrict__ Wr, double* __restrict__ res,
              double tol, int max_sweeps, unsigned int* err, unsigned long long* counters) {
   extern __shared__ double sm64[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), nct = (int)cl.num_blocks();
+  auto csync = [&]() {
+    if (nct > 1) cl.sync();
+    else __syncthreads();
+  };
   // One K x K region: phase A keeps its float32 G32 and W32 there, phase B the float64 W, then
   // G = T W in its place (column by column); E = W^T W - I is kept in Xl (global) until Xl is
   // written at the end.
@@ -273,31 +292,42 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
   int* order = (int*)(rnrm + K);      // K
   unsigned char* sched = (unsigned char*)(order + K);
   __shared__ int flag;
-  float* G32 = (float*)G;
-  float* W32 = G32 + K * K;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int i = e / K, c = e - i * K;
-    G32[c * K + i] = (float)T[i * ldT + c];
-    W32[c * K + i] = (i == c) ? 1.f : 0.f;
-  }
+  // CTA 0's arrays as every CTA of the cluster addresses them
+  double* G0 = nct > 1 ? cl.map_shared_rank(G, 0) : G;
+  double* nrm0 = nct > 1 ? cl.map_shared_rank(nrm, 0) : nrm;
   build_schedule(sched, K);
-  __syncthreads();
-  // A. float32 sweeps (the float32 rounding level of the angles)
-  const int sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
-  // W (float64) <- W32, in place: W[e] overwrites W32 entries of smaller index only, so chunks of
-  // one entry per thread are read, then written
-  double* W = G;
-  for (int e0 = 0; e0 < K * K; e0 += blockDim.x) {
-    const int e = e0 + threadIdx.x;
-    const float v = e < K * K ? W32[e] : 0.f;
+  int sweeps_a = 0;
+  if (rank == 0) {
+    float* G32 = (float*)G;
+    float* W32 = G32 + K * K;
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+      const int i = e / K, c = e - i * K;
+      G32[c * K + i] = (float)T[i * ldT + c];
+      W32[c * K + i] = (i == c) ? 1.f : 0.f;
+    }
     __syncthreads();
-    if (e < K * K) W[e] = (double)v;
-    __syncthreads();
+    // A. float32 sweeps (the float32 rounding level of the angles)
+    sweeps_a = jacobi_sweeps<float, JR, true>(G32, W32, sched, K, 2e-6f, max_sweeps, &flag);
+    // W (float64) <- W32, in place: W[e] overwrites W32 entries of smaller index only, so chunks of
+    // one entry per thread are read, then written
+    for (int e0 = 0; e0 < K * K; e0 += blockDim.x) {
+      const int e = e0 + threadIdx.x;
+      const float v = e < K * K ? W32[e] : 0.f;
+      __syncthreads();
+      if (e < K * K) G[e] = (double)v;
+      __syncthreads();
+    }
   }
+  csync();
+  double* W = G0;
+  // work of the float64 phases spread over the cluster's threads / warps
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int gtid = rank * blockDim.x + threadIdx.x, gthreads = nct * blockDim.x;
+  const int gwarp = rank * nw + warp, gwarps = nct * nw;
   // B1. E = W^T W - I (into Xl, global, symmetric), then W <- W (I - E / 2) row by row (a row of the
   // new W needs only the same row of the old one)
   double* E = Xl;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+  for (int e = gtid; e < K * K; e += gthreads) {
     const int p = e / K, q = e - p * K;
     if (q < p) continue;
     const double* wp = W + p * K;
@@ -305,18 +335,17 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
     double s0 = 0.0, s1 = 0.0;
     int i = 0;
     for (; i + 1 < K; i += 2) {
-      s0 += wp[i] * wq[i];
-      s1 += wp[i + 1] * wq[i + 1];
+      s0 = fma(wp[i], wq[i], s0);
+      s1 = fma(wp[i + 1], wq[i + 1], s1);
     }
-    if (i < K) s0 += wp[i] * wq[i];
+    if (i < K) s0 = fma(wp[i], wq[i], s0);
     const double v = (s0 + s1) - (p == q ? 1.0 : 0.0);
     E[q * K + p] = v;
     E[p * K + q] = v;
   }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  csync();
   constexpr int NT = (JMAXK + 31) / 32;
-  for (int i = warp; i < K; i += nw) {
+  for (int i = gwarp; i < K; i += gwarps) {
     double wi[NT];
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
@@ -346,10 +375,10 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
       if (c < K) W[c * K + i] = out[t];
     }
   }
-  __syncthreads();
+  csync();
   // B2. G = T W, one column per warp in place (T block upper triangular: row i has no entries left
   // of its diagonal block)
-  for (int c = warp; c < K; c += nw) {
+  for (int c = gwarp; c < K; c += gwarps) {
     const double* wc = W + c * K;
     double g[NT];
 #pragma unroll
@@ -360,10 +389,10 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
         const double* trow = T + (long long)i * ldT;
         int k = (i / b) * b;
         for (; k + 1 < K; k += 2) {
-          s0 += trow[k] * wc[k];
-          s1 += trow[k + 1] * wc[k + 1];
+          s0 = fma(trow[k], wc[k], s0);
+          s1 = fma(trow[k + 1], wc[k + 1], s1);
         }
-        if (k < K) s0 += trow[k] * wc[k];
+        if (k < K) s0 = fma(trow[k], wc[k], s0);
       }
       g[t] = s0 + s1;
     }
@@ -371,90 +400,98 @@ k_jacobi_f64(const double* __restrict__ T, int ldT, int K, const double* __restr
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       const int i = lane + 32 * t;
-      if (i < K) G[c * K + i] = g[t];
+      if (i < K) G0[c * K + i] = g[t];
     }
   }
-  __syncthreads();
+  csync();
   // B3. float64 sweeps from the float32-level angles on G alone (tracked column norms); the right
   // vectors are formed afterwards from T^T
-  for (int c = warp; c < K; c += nw) {
+  for (int c = gwarp; c < K; c += gwarps) {
     double s2 = 0.0;
-    for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
+    for (int i = lane; i < K; i += 32) s2 = fma(G0[c * K + i], G0[c * K + i], s2);
     s2 = warp_sum(s2);
-    if (lane == 0) nrm[c] = s2;
+    if (lane == 0) nrm0[c] = s2;
   }
-  __syncthreads();
-  int sweeps_b;
-  if constexpr (JR <= 6)
-    sweeps_b = jacobi_sweeps<double, 2 * JR, false, true, JL / 2>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
-  else
-    sweeps_b = jacobi_sweeps<double, JR, false, true, JL>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
-  const int sweeps = sweeps_a + sweeps_b;
-  if (threadIdx.x == 0) {
-    if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
-    if (counters) {
-      atomicAdd(&counters[0], 1ULL);
-      atomicAdd(&counters[1], (unsigned long long)sweeps);
+  csync();
+  int sweeps_b = 0;
+  if (rank == 0) {
+    if constexpr (JR <= 6)
+      sweeps_b = jacobi_sweeps<double, 2 * JR, false, true, JL / 2>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
+    else
+      sweeps_b = jacobi_sweeps<double, JR, false, true, JL>(G, G, sched, K, tol, max_sweeps, &flag, true, nrm);
+    const int sweeps = sweeps_a + sweeps_b;
+    if (threadIdx.x == 0) {
+      if (sweeps_a > max_sweeps || sweeps_b > max_sweeps) svt_set_error(err, SVT_DEVERR_JACOBI);
+      if (counters) {
+        atomicAdd(&counters[0], 1ULL);
+        atomicAdd(&counters[1], (unsigned long long)sweeps);
+      }
     }
-  }
-  // column norms (one warp per column)
-  for (int c = warp; c < K; c += nw) {
-    double s2 = 0.0;
-    for (int i = lane; i < K; i += 32) s2 += G[c * K + i] * G[c * K + i];
-    s2 = warp_sum(s2);
-    if (lane == 0) {
-      const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
-      nrm[c] = th;
-      rnrm[c] = th > 0.0 ? rcp_nr(th) : 0.0;
+    // column norms (one warp per column)
+    for (int c = warp; c < K; c += nw) {
+      double s2 = 0.0;
+      for (int i = lane; i < K; i += 32) s2 = fma(G[c * K + i], G[c * K + i], s2);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        const double th = s2 > 0.0 ? s2 * rsqrt_nr(s2, 2) : 0.0;
+        nrm[c] = th;
+        rnrm[c] = th > 0.0 ? rcp_nr(th) : 0.0;
+      }
     }
+    __syncthreads();
+    sort_columns<double>(nrm, order, K);
+    __syncthreads();
+    for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+      const int i = e / K, k = e - i * K;
+      const int c = order[k];
+      Xl[i * K + k] = G[c * K + i] * rnrm[c];
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) theta[k] = nrm[order[k]];
   }
-  __syncthreads();
-  sort_columns<double>(nrm, order, K);
-  __syncthreads();
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
-    const int i = e / K, k = e - i * K;
-    const int c = order[k];
-    Xl[i * K + k] = G[c * K + i] * rnrm[c];
-  }
-  for (int k = threadIdx.x; k < K; k += blockDim.x) theta[k] = nrm[order[k]];
+  csync();
+  const double* rn0 = nct > 1 ? cl.map_shared_rank(rnrm, 0) : rnrm;
+  const int* ord0 = nct > 1 ? cl.map_shared_rank(order, 0) : order;
   // right vectors of the leading nv triplets: w_k = T^T x_k / theta_k = T^T g_k / theta_k^2 (column
   // i of T has no entries below its diagonal block); the others are not used by the solver and are
   // left zero
   if (nv > K) nv = K;
-  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+  for (int e = gtid; e < K * K; e += gthreads) {
     const int i = e / K, k = e - i * K;
     double v = 0.0;
     if (k < nv) {
-      const int c = order[k];
-      const double* gc = G + c * K;
+      const int c = ord0[k];
+      const double* gc = G0 + c * K;
       const int rend = min(K, (i / b + 1) * b);
       double s0 = 0.0, s1 = 0.0;
       int r = 0;
       for (; r + 1 < rend; r += 2) {
-        s0 += T[(long long)r * ldT + i] * gc[r];
-        s1 += T[(long long)(r + 1) * ldT + i] * gc[r + 1];
+        s0 = fma(T[(long long)r * ldT + i], gc[r], s0);
+        s1 = fma(T[(long long)(r + 1) * ldT + i], gc[r + 1], s1);
       }
-      if (r < rend) s0 += T[(long long)r * ldT + i] * gc[r];
-      v = (s0 + s1) * (rnrm[c] * rnrm[c]);
+      if (r < rend) s0 = fma(T[(long long)r * ldT + i], gc[r], s0);
+      const double rc = rn0[c];
+      v = (s0 + s1) * (rc * rc);
     }
     Wr[i * K + k] = v;
   }
   // residual estimates, one warp per triplet
-  for (int k = warp; k < K; k += nw) {
+  for (int k = gwarp; k < K; k += gwarps) {
     double r2 = 0.0;
     if (S) {
-      const int c = order[k];
-      const double inv = rnrm[c];
+      const int c = ord0[k];
+      const double inv = rn0[c];
       for (int e = lane; e < b; e += 32) {
         double v = 0.0;
-        for (int d = e; d < b; ++d) v += S[e * b + d] * G[c * K + (K - b + d)];
+        for (int d = e; d < b; ++d) v = fma(S[e * b + d], G0[c * K + (K - b + d)], v);
         v *= inv;
-        r2 += v * v;
+        r2 = fma(v, v, r2);
       }
       r2 = warp_sum(r2);
     }
     if (lane == 0) res[k] = sqrt(r2);
   }
+  // CTA 0's shared memory is read until here
+  csync();
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -647,6 +684,57 @@ bool jacobi_attrs() {
   return state == 1;
 }
 
+// CTAs of the cluster that runs the float64 projected SVD (1 where a cluster launch is not possible).
+static constexpr int kJacobiCluster = 8;
+
+template <int JR>
+static int jacobi_f64_cluster_size(size_t smem_max) {
+  static std::once_flag once;
+  static int size = 1;
+  std::call_once(once, [smem_max] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kJacobiCluster);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem_max;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kJacobiCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_jacobi_f64<JR>, &cfg) == cudaSuccess && nclusters > 0)
+      size = kJacobiCluster;
+    (void)cudaGetLastError();
+  });
+  return size;
+}
+
+template <int JR>
+static int jacobi_f64_launch(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta,
+                             double* Xl, double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
+                             unsigned long long* counters, size_t smem, int thr, cudaStream_t st) {
+  const size_t mx64 = (size_t)(JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
+  const int nct = jacobi_f64_cluster_size<JR>(mx64);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nct);
+  cfg.blockDim = dim3(thr);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = nct;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = nct > 1 ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_jacobi_f64<JR>, T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err,
+                            counters) == cudaSuccess
+             ? 1
+             : 0;
+}
+
 int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta, double* Xl,
                      double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
                      unsigned long long* counters, cudaStream_t st) {
@@ -655,14 +743,13 @@ int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, in
   const int thr = jacobi_threads(K);
   const int rpl = (K + JL - 1) / JL;
 #define SVT_JF64(JRV) \
-  k_jacobi_f64<JRV><<<1, thr, smem, st>>>(T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err, counters)
-  if (rpl <= 3) SVT_JF64(3);
-  else if (rpl <= 6) SVT_JF64(6);
-  else if (rpl <= 9) SVT_JF64(9);
-  else if (rpl <= 12) SVT_JF64(12);
-  else SVT_JF64(16);
+  jacobi_f64_launch<JRV>(T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err, counters, smem, thr, st)
+  if (rpl <= 3) return SVT_JF64(3);
+  if (rpl <= 6) return SVT_JF64(6);
+  if (rpl <= 9) return SVT_JF64(9);
+  if (rpl <= 12) return SVT_JF64(12);
+  return SVT_JF64(16);
 #undef SVT_JF64
-  return 1;
 }
 
 int launch_small_svd_mixed(const double* T, int ldT, int K, const double* S, int b, double* theta, double* Xl,

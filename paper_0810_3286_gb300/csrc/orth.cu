@@ -128,7 +128,7 @@ __device__ void gram_chunk(const double* __restrict__ Q, long long q_stride, int
           c += nq * b;
         }
         double s = acc[k];
-        for (int rr = 0; rr < nr; ++rr) s += tile[rr][c] * tile[rr][nq * b + d];
+        for (int rr = 0; rr < nr; ++rr) s = fma(tile[rr][c], tile[rr][nq * b + d], s);
         acc[k] = s;
       }
     }
@@ -330,12 +330,12 @@ __device__ void update_rows(int mode, const double* __restrict__ Q, long long q_
         const double* ccol = sC + blk * b * b + d;
         int c = 0;
         for (; c + 3 < b; c += 4) {
-          a0 += qrow[c] * ccol[c * b];
-          a1 += qrow[c + 1] * ccol[(c + 1) * b];
-          a2 += qrow[c + 2] * ccol[(c + 2) * b];
-          a3 += qrow[c + 3] * ccol[(c + 3) * b];
+          a0 = fma(qrow[c], ccol[c * b], a0);
+          a1 = fma(qrow[c + 1], ccol[(c + 1) * b], a1);
+          a2 = fma(qrow[c + 2], ccol[(c + 2) * b], a2);
+          a3 = fma(qrow[c + 3], ccol[(c + 3) * b], a3);
         }
-        for (; c < b; ++c) a0 += qrow[c] * ccol[c * b];
+        for (; c < b; ++c) a0 = fma(qrow[c], ccol[c * b], a0);
       }
       v = P[(long long)i * b + d] - ((a0 + a1) + (a2 + a3));
     }

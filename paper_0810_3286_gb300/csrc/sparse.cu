@@ -40,7 +40,7 @@ template <typename XT, typename AT, int CPL>
 __device__ __forceinline__ void spmm_fma(AT (&acc)[CPL], AT v, const XT* __restrict__ src) {
   const typename XRow<XT>::V x = __ldg(reinterpret_cast<const typename XRow<XT>::V*>(src));
 #pragma unroll
-  for (int q = 0; q < CPL; ++q) acc[q] += v * (AT)xcomp(x, q);
+  for (int q = 0; q < CPL; ++q) acc[q] = fmac(v, (AT)xcomp(x, q), acc[q]);
 }
 
 // The segments s0 .. s0 + (SPMM_T / 32) / WPR - 1 of one product, by the whole CTA.
@@ -301,8 +301,8 @@ __device__ __forceinline__ void upd_row(int i, int lane, const int32_t* __restri
     for (int t = 0; t < RMAX; ++t) {
       if (t >= r) break;
       AT ut = t < 32 ? __shfl_sync(0xffffffffu, u0, t) : __shfl_sync(0xffffffffu, u1, t - 32);
-      if (t & 1) x1 += ut * (AT)vr[t];
-      else x0 += ut * (AT)vr[t];
+      if (t & 1) x1 = fmac(ut, (AT)vr[t], x1);
+      else x0 = fmac(ut, (AT)vr[t], x0);
     }
     if (live) {
       AT ev = mp - (x0 + x1);
