@@ -1,28 +1,51 @@
 """Full-size rank-10 workloads of Table 1 (Sec. 5.2.1) on the float32 path, checked by properties
-that hold at any size (no oracle run at these sizes).
+that hold at any size (no oracle run inside the test).
 
 Table 1 averages five random instances per row; here five seeds per shape are solved with
 tau = 5n, delta = 1.2/p, eps = 1e-4 (eq. (5.5)), and:
 
-* the median iteration count is within +-15% of the paper's value for that row (123 at
-  10000 x 10000, 124 at 20000 x 20000, 125 at 30000 x 30000);
+* the mean iteration count over the instances is within +-15% of the paper's value for that row
+  (123 at 10000 x 10000, 124 at 20000 x 20000, 125 at 30000 x 30000).  An instance is left out of
+  the mean only when a committed trace of the float64 sparse-tier oracle (tests/golden/, written
+  by make_tierb_trace.py from the oracle alone) shows that the iteration itself needs more than
+  1.15 times the paper's count on it (seed 4 at 10000 x 10000, seeds 0 and 2 at 30000 x 30000: an
+  (r+1)-th singular value of the dual iterate hovers at tau and the rank briefly rises to r + 1);
+  such instances are followed iterate by iterate against their trace in
+  test_gpu_slow_instances.py;
 * every instance that converges within the paper's count (+15%) ends at the planted rank (the
-  slow ones at r or r + 1), and every instance that meets the stopping rule has relative error ||X - M||_F / ||M||_F (eq. (5.8), closed form from the factors) below the 2e-4
-  the paper reports for all of Table 1;
+  slow ones at r or r + 1), and every instance that meets the stopping rule has relative error
+  ||X - M||_F / ||M||_F (eq. (5.8), closed form from the factors) below the 2e-4 the paper reports
+  for all of Table 1;
 * on one converged instance the final shrink satisfies the certificate of Theorem 2.1: with
   X = D_tau(Y) = U diag(sigma - tau) V^T, (Y - X) V = tau U on the kept singular vectors, where
   Y V comes from the library's own sparse product.
-
-The median, not the mean, is compared: a minority of instances (one in five at 10000^2 and two in
-five at 30000^2 with seeds 0-4) converge much more slowly because an (r+1)-th singular value of
-the dual iterate hovers at tau and the rank briefly rises to r+1; an independent float64 SVT
-with ARPACK partial SVDs reproduces those traces, so it is a property of the iteration on those
-instances, not of this implementation.
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
 from svt_inputs import planted_problem, sample_count
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+sys.path.insert(0, GOLDEN)
+from make_tierb_trace import read_trace  # noqa: E402
+
+WORKLOAD = {10000: "single_10000", 30000: "large_30000"}
+
+
+def _oracle_slow(n, seed, paper_iters):
+    """True when the committed oracle trace of this instance needs more than 1.15x the paper's count
+    (it did not stop by then); False when there is no such trace."""
+    if n not in WORKLOAD:
+        return False
+    path = os.path.join(GOLDEN, "tierb_trace_%s_seed%d.txt" % (WORKLOAD[n], seed))
+    if not os.path.exists(path):
+        return False
+    head, _, rows = read_trace(path)
+    limit = int(1.15 * paper_iters)
+    return len(rows) > limit and all(res > float(head["eps"]) for k, _, _, _, res, _ in rows if k <= limit)
 
 pytestmark = pytest.mark.gpu
 
@@ -75,8 +98,11 @@ def test_table1_rank10_rows(cuda, n, paper_iters):
                     # that update moves Y V by at most delta * eps * ||P_Omega M||_F
                     assert _certificate(torch, s, U, d, V, p.tau_default()) < 1e-3, seed
                     checked = True
-    med = float(np.median(iters))
-    assert 0.85 * paper_iters <= med <= 1.15 * paper_iters, iters
+    kept = [it for sd, it in zip(SEEDS, iters) if not _oracle_slow(n, sd, paper_iters)]
+    assert len(kept) >= 3, iters
+    mean = float(np.mean(kept))
+    print("n = %d: iterations %s, mean over the instances kept %.1f" % (n, iters, mean))
+    assert 0.85 * paper_iters <= mean <= 1.15 * paper_iters, iters
     assert checked, iters
 
 
