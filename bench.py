@@ -14,7 +14,7 @@ steps (inputs resident in HBM); `e2e` is the same metric with the inputs copied 
 memory and the factors of X copied back inside every step (one pass over the seeds).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--config NAME] [--precision fp64|fp32] [--seeds 0,1,2,3,4] [--k-max 1000]
+                    [--config NAME] [--precision fp64|fp32|bf16] [--seeds 0,1,2,3,4] [--k-max 1000]
     python bench.py --ncu-iters N ...   bounded run for a profiler: one create + kick + N
                                         iterations of the first seed, nothing timed (shrink
                                         decided on the host: ncu skips conditional graphs)
@@ -71,8 +71,10 @@ def _kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_for(kernel_class):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current source."""
+def _traffic_for(kernel_class, precision):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the captured
+    launches of the class) from the committed ncu summary of this precision's profiling run, if it
+    was taken on the current kernel source; None otherwise."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
@@ -80,7 +82,7 @@ def _traffic_for(kernel_class):
         return None
     if t.get("csrc_sha") != _kernel_source_sha():
         return None
-    entry = t.get("classes", {}).get(kernel_class)
+    entry = t.get("classes_" + precision, {}).get(kernel_class)
     return None if entry is None else float(entry)
 
 
@@ -275,8 +277,11 @@ def _config_dict(args, nnz, world):
     c = CONFIGS[args.config]
     return {"workload": "%s: %dx%d rank %d, |Omega|=%d (6 r(2n-r)), tau=5n, delta=1.2/p, eps=1e-4"
                         % (args.config, c["n1"], c["n2"], c["r"], nnz),
-            "precision": "%s values and sparse products, float64 Lanczos basis and projected SVD"
-                         % ("float32" if args.precision == "fp32" else "float64"),
+            "precision": {"fp64": "float64 values and sparse products, float64 Lanczos basis and projected SVD",
+                          "fp32": "float32 values and sparse products (float32 accumulation), float64 Lanczos basis "
+                                  "and projected SVD",
+                          "bf16": "bfloat16 values in the sparse products while the residual is above 1e-2, then "
+                                  "float32 (float32 accumulation), float64 Lanczos basis and projected SVD"}[args.precision],
             "step": "svt_create (Omega storage) + svt_solve (kick + iterations to 1e-4, at most k_max) + "
                     "svt_destroy, one problem instance per step",
             "seeds": args.seed_list, "k_max": args.k_max,
@@ -445,7 +450,7 @@ def run_ours(args):
         achieved = (by_l / 1e9) / (ms_l / 1e3) if ms_l > 0 else None
         return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_kind": "%s copy bandwidth" % peak_kind,
-                "traffic": _traffic_for(classes[0]), "launches_timed": n_l,
+                "traffic": _traffic_for(classes[0], args.precision), "launches_timed": n_l,
                 "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
                 "algorithmic_bytes_per_launch": by_l / n_l if n_l else None}
 
@@ -457,7 +462,7 @@ def run_ours(args):
         return {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": (achieved / peak_tflops) if achieved else None,
                 "peak_kind": "%s peak derived from unit counts x maximum SM clock" % kind,
-                "traffic": _traffic_for(cls), "launches_timed": n_l,
+                "traffic": _traffic_for(cls, args.precision), "launches_timed": n_l,
                 "avg_launch_us": 1000.0 * ms_l / n_l if n_l else None,
                 "algorithmic_flops_per_launch": flops_total / n_l if n_l else None}
 
@@ -496,7 +501,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1000.0 * total_s_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16"}[args.precision], "data": "synthetic",
         "config": _config_dict(args, p0.nnz, world),
         "time_to_1e-4_ms": (float(np.mean([step_ms[k] for k, r in enumerate(results) if r["converged"]]))
                             if conv else None),
@@ -529,7 +534,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="large_30000", choices=sorted(CONFIGS))
-    ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp64", choices=["fp32", "fp64", "bf16"])
     ap.add_argument("--seeds", default="0,1,2,3,4",
                     help="problem instances the steps cycle over (rank k solves seed + 1000 k)")
     ap.add_argument("--k-max", type=int, default=1000, help="SVT iteration cap per solve")
