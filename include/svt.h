@@ -136,6 +136,10 @@ typedef struct svt_options {
                              float64, so the basis stays orthonormal to float64 rounding.  0 (default): on
                              for FP32 / BF16 values, off for FP64; 1: on; -1: off.  Needs orth_repass >= 0
                              (off otherwise) */
+  int jacobi_cluster;     /* FP64 projected SVD: 0 (default) a thread-block cluster of 8 CTAs where the device
+                             allows it (the dense products, right vectors and residual estimates spread over
+                             the cluster), else one CTA; 1: always one CTA (the same arithmetic but for the
+                             grouping of sums) */
 } svt_options;
 
 /* Per-iteration record (Algorithm 1, one pass of the for-loop body). */

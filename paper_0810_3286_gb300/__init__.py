@@ -74,7 +74,8 @@ class Solver:
                  max_cycles: int = 40, use_graphs: bool = True, fused_orth: bool = True, block: int = 0,
                  restart_steps: int = 0, bf16_switch: float = 1e-2, orth_grid: int = 0, orth_repass: float = 0.0,
                  allocator=None, shrink_engine: str = "lanczos", rsvd_oversample: int = 8, rsvd_power: int = 1,
-                 rsvd_seed: int = 0, device_loop: bool = True, orth_tf32: Optional[bool] = None):
+                 rsvd_seed: int = 0, device_loop: bool = True, orth_tf32: Optional[bool] = None,
+                 jacobi_cluster: int = 0):
         L = library()
         opt = svt_options()
         L.svt_default_options(ctypes.byref(opt))
@@ -98,6 +99,7 @@ class Solver:
         opt.rsvd_seed = int(rsvd_seed) & (2**64 - 1)
         opt.device_loop = 1 if device_loop else 0
         opt.orth_tf32 = 0 if orth_tf32 is None else (1 if orth_tf32 else -1)
+        opt.jacobi_cluster = jacobi_cluster
         if allocator is not None:
             # (alloc(bytes) -> int device pointer or 0, free(ptr)); the ctypes thunks must outlive
             # the context

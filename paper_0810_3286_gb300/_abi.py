@@ -65,6 +65,7 @@ class svt_options(ctypes.Structure):
         ("rsvd_seed", ctypes.c_uint64),
         ("device_loop", ctypes.c_int),
         ("orth_tf32", ctypes.c_int),
+        ("jacobi_cluster", ctypes.c_int),
     ]
 
 

@@ -631,7 +631,7 @@ static svt_status cycle_end(svt_ctx* c, int b, int J, int nk, bool copy_out) {
   l += prof_launch(c, SVT_PROF_JACOBI, 24.0 * K * K, [&] {
     if (c->prec == SVT_FP64)
       return launch_small_svd(c->T, kKMax, K, c->Rkeep, b, nvec, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
-                              c->dcount, c->st);
+                              c->dcount, c->st, c->opt.jacobi_cluster);
     return launch_small_svd_mixed(c->T, kKMax, K, c->Rkeep, b, c->theta, c->Xl, c->Wr, c->res, nvec, c->wsrc, 2e-6,
                                   60, c->err, c->dcount, c->st);
   });
@@ -1005,7 +1005,7 @@ static svt_status shrink_randomized(svt_ctx* c, double tau, int s_init, int* r_o
     int lj = prof_launch(c, SVT_PROF_JACOBI, 24.0 * l * l, [&] {
       if (c->prec == SVT_FP64)
         return launch_small_svd(c->T, kKMax, l, nullptr, l, l, c->theta, c->Xl, c->Wr, c->res, tol_j, 60, c->err,
-                                c->dcount, c->st);
+                                c->dcount, c->st, c->opt.jacobi_cluster);
       return launch_small_svd_mixed(c->T, kKMax, l, nullptr, l, c->theta, c->Xl, c->Wr, c->res, l, c->wsrc, 2e-6, 60,
                                     c->err, c->dcount, c->st);
     });
@@ -1091,6 +1091,7 @@ extern "C" void svt_default_options(svt_options* opt) {
   opt->rsvd_seed = 0;
   opt->device_loop = 1;
   opt->orth_tf32 = 0;
+  opt->jacobi_cluster = 0;
 }
 
 extern "C" const char* svt_last_error(const svt_ctx* ctx) {
@@ -1356,6 +1357,7 @@ extern "C" svt_status svt_create(int64_t m, int64_t n, int64_t nnz, const int32_
   if (o.precision == SVT_BF16 && !(o.bf16_switch >= 0.0)) return fail(nullptr, SVT_ERR_ARG, "bf16_switch must be >= 0");
   if (o.orth_grid < 0) return fail(nullptr, SVT_ERR_ARG, "orth_grid must be >= 0");
   if (!(o.orth_repass == o.orth_repass)) return fail(nullptr, SVT_ERR_ARG, "orth_repass is NaN");
+  if (o.jacobi_cluster != 0 && o.jacobi_cluster != 1) return fail(nullptr, SVT_ERR_ARG, "jacobi_cluster must be 0 or 1");
   if ((o.device_alloc == nullptr) != (o.device_free == nullptr))
     return fail(nullptr, SVT_ERR_ARG, "device_alloc and device_free must be given together");
   if (o.shrink_engine != SVT_SHRINK_LANCZOS && o.shrink_engine != SVT_SHRINK_RANDOMIZED)

@@ -135,9 +135,10 @@ int launch_orth_coop(double* P, const double* Q, long long q_stride, int nq, int
 // row-major (only the first nv columns of Wr are formed, the others are zero).  Also res[i] = || S (Xl rows [K-b, K), column i) ||
 // for the b x b block S (upper triangular, may be NULL -> res = 0).
 // counters[0] += 1, counters[1] += sweeps.
+// cluster: CTAs of the launch (0: a cluster of 8 where the device allows it, 1: one CTA).
 int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta, double* Xl,
                      double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
-                     unsigned long long* counters, cudaStream_t st);
+                     unsigned long long* counters, cudaStream_t st, int cluster = 0);
 
 // Self-tests of the Newton helpers (out: 5 doubles per input): slots 0..3 rcp (2 steps, 1 step),
 // rsqrt (2 steps, 1 step) of jacobi.cu; slot 4 the pivot rsqrt of orth.cu.

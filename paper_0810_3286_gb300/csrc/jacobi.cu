@@ -714,9 +714,9 @@ static int jacobi_f64_cluster_size(size_t smem_max) {
 template <int JR>
 static int jacobi_f64_launch(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta,
                              double* Xl, double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
-                             unsigned long long* counters, size_t smem, int thr, cudaStream_t st) {
+                             unsigned long long* counters, size_t smem, int thr, cudaStream_t st, int cluster) {
   const size_t mx64 = (size_t)(JMAXK * JMAXK + 2 * JMAXK) * sizeof(double) + JMAXK * sizeof(int) + sched_bytes(JMAXK);
-  const int nct = jacobi_f64_cluster_size<JR>(mx64);
+  const int nct = cluster == 1 ? 1 : jacobi_f64_cluster_size<JR>(mx64);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nct);
   cfg.blockDim = dim3(thr);
@@ -737,13 +737,14 @@ static int jacobi_f64_launch(const double* T, int ldT, int K, const double* S, i
 
 int launch_small_svd(const double* T, int ldT, int K, const double* S, int b, int nv, double* theta, double* Xl,
                      double* Wr, double* res, double tol, int max_sweeps, unsigned int* err,
-                     unsigned long long* counters, cudaStream_t st) {
+                     unsigned long long* counters, cudaStream_t st, int cluster) {
   if (!jacobi_attrs() || K > JMAXK) return 0;  // no launch; the caller's checks report the failure
   const size_t smem = (size_t)(K * K + 2 * K) * sizeof(double) + (size_t)K * sizeof(int) + sched_bytes(K);
   const int thr = jacobi_threads(K);
   const int rpl = (K + JL - 1) / JL;
 #define SVT_JF64(JRV) \
-  jacobi_f64_launch<JRV>(T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err, counters, smem, thr, st)
+  jacobi_f64_launch<JRV>(T, ldT, K, S, b, nv, theta, Xl, Wr, res, tol, max_sweeps, err, counters, smem, thr, st, \
+                         cluster)
   if (rpl <= 3) return SVT_JF64(3);
   if (rpl <= 6) return SVT_JF64(6);
   if (rpl <= 9) return SVT_JF64(9);

@@ -99,13 +99,14 @@ def test_parity_fp64_ragged_rectangular(cuda):
 
 
 @pytest.mark.parametrize("variant", [{"fused_orth": False}, {"use_graphs": False}, {"orth_grid": 8},
-                                     {"device_loop": False}, {"orth_tf32": True}])
+                                     {"device_loop": False}, {"orth_tf32": True}, {"jacobi_cluster": 1}])
 def test_parity_fp64_other_launch_paths(cuda, variant):
     """The eight-kernel orthonormalisation (fused_orth = 0, the path taken without cooperative
     launches), kernel-by-kernel launches without CUDA graphs, a small cooperative grid, the shrink
-    decided on the host after every Lanczos cycle (device_loop = 0), and the first Gram-Schmidt
-    pass on the tensor cores (orth_tf32, off by default in float64) give the same iterates as the
-    oracle."""
+    decided on the host after every Lanczos cycle (device_loop = 0), the first Gram-Schmidt pass
+    on the tensor cores (orth_tf32, off by default in float64), and the projected SVD in one CTA
+    (jacobi_cluster = 1, the form taken where a cluster launch is not possible) give the same
+    iterates as the oracle."""
     p = planted_problem(173, 131, 3, 3 * 5 * (173 + 131 - 3), seed=12)
     tau, delta = p.tau_default(), p.delta_default()
     ref = osvt.svt(p.n1, p.n2, p.rows, p.cols, p.vals, tau, delta, k_max=25, eps=1e-4)
