@@ -2037,169 +2037,183 @@ extern "C" svt_status svt_batch_solve(svt_ctx* const* jobs, int n, const double*
   CU(c0, cudaMemsetAsync(berr, 0, sizeof(unsigned int), bst));
   int64_t batch_launches = 0;
   auto drop = [&](std::vector<int>& v, int i) { v.erase(std::find(v.begin(), v.end(), i)); };
+  // a launch failure leaves the batch's streams unusable: every unfinished job reports it
+  auto abort_all = [&](svt_status st) {
+    for (int i : alive) status[i] = st;
+    return st;
+  };
 
-  while (!alive.empty()) {
-    // ---- shrink of every unfinished job: lockstep Lanczos cycles ----
-    std::vector<ShrinkRun> R(n);
-    std::vector<std::vector<double>> th(n);
-    std::vector<int> sh_s(n), sh_passes(n), sh_b(n), sh_J(n), j0(n);
-    std::vector<int> shrinking;
-    for (int i : std::vector<int>(alive)) {
-      svt_ctx* c = jobs[i];
-      const int kmin = (int)std::min(c->m, c->n);
-      const svt_status st = shrink_start(c, R[i], std::min(c->r + 1, kmin), c->tau, false);
-      if (st != SVT_OK) {
-        status[i] = st;
-        drop(alive, i);
-      } else {
-        shrinking.push_back(i);
-      }
-    }
-    while (!shrinking.empty()) {
-      int Jmax = 0;
-      for (int i : std::vector<int>(shrinking)) {
-        const svt_status st = cycle_begin(jobs[i], R[i].b, R[i].J, R[i].thick, R[i].Jprev, R[i].nk, &j0[i]);
+  // every return inside the loop is a failure of the batch's launches or streams (a job's own
+  // failure is recorded in status[] and the job leaves); the jobs still running then report it
+  auto run = [&]() -> svt_status {
+    while (!alive.empty()) {
+      // ---- shrink of every unfinished job: lockstep Lanczos cycles ----
+      std::vector<ShrinkRun> R(n);
+      std::vector<std::vector<double>> th(n);
+      std::vector<int> sh_s(n), sh_passes(n), sh_b(n), sh_J(n), j0(n);
+      std::vector<int> shrinking;
+      for (int i : std::vector<int>(alive)) {
+        svt_ctx* c = jobs[i];
+        const int kmin = (int)std::min(c->m, c->n);
+        const svt_status st = shrink_start(c, R[i], std::min(c->r + 1, kmin), c->tau, false);
         if (st != SVT_OK) {
           status[i] = st;
-          drop(shrinking, i);
           drop(alive, i);
-          continue;
-        }
-        Jmax = std::max(Jmax, R[i].J);
-      }
-      for (int j = 0; j < Jmax; ++j) {
-        std::vector<int> L;
-        for (int i : shrinking)
-          if (j >= j0[i] && j < R[i].J) L.push_back(i);
-        if (L.empty()) continue;
-        for (int side = 0; side < 2; ++side) {
-          const bool left = side == 0;
-          std::vector<SpmmJob> sj;
-          for (int i : L) {
-            SpmmJob J = cycle_spmm_job(jobs[i], R[i].b, j, left);
-            if (bo.autotune) J.wpr = tuned_wpr(jobs[i], J, prec, left, bst);
-            sj.push_back(J);
-          }
-          TRY(batch_after_jobs(L));
-          if (launch_spmm_jobs(prec, sj.data(), (int)sj.size(), bo.spmm_grid, bst) != 1)
-            return fail(c0, SVT_ERR_CUDA, "batched sparse product launch failed: %s",
-                        cudaGetErrorString(cudaGetLastError()));
-          ++batch_launches;
-          TRY(jobs_after_batch(L));
-          for (int i : L) {
-            const int nspmm = 1;
-            jobs[i]->last_spmm += nspmm;
-            jobs[i]->total_spmm += nspmm;
-            const svt_status st = left ? cycle_orth_left(jobs[i], R[i].b, j)
-                                       : cycle_orth_right(jobs[i], R[i].b, j, R[i].J);
-            if (st != SVT_OK) return st;   // a launch failed: the batch stream is unusable
-          }
+        } else {
+          shrinking.push_back(i);
         }
       }
-      for (int i : shrinking) {
-        svt_ctx* c = jobs[i];
-        TRY(cycle_end(c, R[i].b, R[i].J, R[i].nk, true));
-        c->last_cycles += 1;
-        c->total_cycles += 1;
-        unsigned int* herr = reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1);
-        CU(c, cudaMemcpyAsync(herr, c->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
-      }
-      if (conc) {
-        for (int i : shrinking) CU(jobs[i], cudaStreamSynchronize(jobs[i]->st));
-      } else {
-        CU(c0, cudaStreamSynchronize(bst));
-      }
-      for (int i : std::vector<int>(shrinking)) {
-        svt_ctx* c = jobs[i];
-        prof_harvest(c);
-        svt_status st = check_err_word(c, *reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1));
-        if (st == SVT_OK) {
-          double defect = 0.0;
-          std::memcpy(&defect, c->h_pin + 3 * kKMax + 1, sizeof defect);
-          if (defect > 1e-6) c->two_corrections = true;
-          bool done = false;
-          st = shrink_advance(c, R[i], c->h_pin, c->h_pin + kKMax, &done, th[i], &sh_s[i], &sh_passes[i], &sh_b[i],
-                              &sh_J[i]);
-          if (st == SVT_OK && !done) continue;
+      while (!shrinking.empty()) {
+        int Jmax = 0;
+        for (int i : std::vector<int>(shrinking)) {
+          const svt_status st = cycle_begin(jobs[i], R[i].b, R[i].J, R[i].thick, R[i].Jprev, R[i].nk, &j0[i]);
+          if (st != SVT_OK) {
+            status[i] = st;
+            drop(shrinking, i);
+            drop(alive, i);
+            continue;
+          }
+          Jmax = std::max(Jmax, R[i].J);
+        }
+        for (int j = 0; j < Jmax; ++j) {
+          std::vector<int> L;
+          for (int i : shrinking)
+            if (j >= j0[i] && j < R[i].J) L.push_back(i);
+          if (L.empty()) continue;
+          for (int side = 0; side < 2; ++side) {
+            const bool left = side == 0;
+            std::vector<SpmmJob> sj;
+            for (int i : L) {
+              SpmmJob J = cycle_spmm_job(jobs[i], R[i].b, j, left);
+              if (bo.autotune) J.wpr = tuned_wpr(jobs[i], J, prec, left, bst);
+              sj.push_back(J);
+            }
+            TRY(batch_after_jobs(L));
+            if (launch_spmm_jobs(prec, sj.data(), (int)sj.size(), bo.spmm_grid, bst) != 1)
+              return abort_all(fail(c0, SVT_ERR_CUDA, "batched sparse product launch failed: %s",
+                                    cudaGetErrorString(cudaGetLastError())));
+            ++batch_launches;
+            TRY(jobs_after_batch(L));
+            for (int i : L) {
+              const int nspmm = 1;
+              jobs[i]->last_spmm += nspmm;
+              jobs[i]->total_spmm += nspmm;
+              const svt_status st = left ? cycle_orth_left(jobs[i], R[i].b, j)
+                                         : cycle_orth_right(jobs[i], R[i].b, j, R[i].J);
+              if (st != SVT_OK) return abort_all(st);
+            }
+          }
+        }
+        for (int i : shrinking) {
+          svt_ctx* c = jobs[i];
+          const svt_status se = cycle_end(c, R[i].b, R[i].J, R[i].nk, true);
+          if (se != SVT_OK) return abort_all(se);
+          c->last_cycles += 1;
+          c->total_cycles += 1;
+          unsigned int* herr = reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1);
+          CU(c, cudaMemcpyAsync(herr, c->err, sizeof(unsigned int), cudaMemcpyDeviceToHost, c->st));
+        }
+        if (conc) {
+          for (int i : shrinking) CU(jobs[i], cudaStreamSynchronize(jobs[i]->st));
+        } else {
+          CU(c0, cudaStreamSynchronize(bst));
+        }
+        for (int i : std::vector<int>(shrinking)) {
+          svt_ctx* c = jobs[i];
+          prof_harvest(c);
+          svt_status st = check_err_word(c, *reinterpret_cast<unsigned int*>(c->h_pin + 4 * kKMax - 1));
           if (st == SVT_OK) {
-            int r = 0;
-            st = shrink_finish(c, c->tau, th[i], sh_s[i], sh_passes[i], sh_b[i], sh_J[i], &r);
+            double defect = 0.0;
+            std::memcpy(&defect, c->h_pin + 3 * kKMax + 1, sizeof defect);
+            if (defect > 1e-6) c->two_corrections = true;
+            bool done = false;
+            st = shrink_advance(c, R[i], c->h_pin, c->h_pin + kKMax, &done, th[i], &sh_s[i], &sh_passes[i], &sh_b[i],
+                                &sh_J[i]);
+            if (st == SVT_OK && !done) continue;
+            if (st == SVT_OK) {
+              int r = 0;
+              st = shrink_finish(c, c->tau, th[i], sh_s[i], sh_passes[i], sh_b[i], sh_J[i], &r);
+            }
+          }
+          drop(shrinking, i);
+          if (st != SVT_OK) {
+            status[i] = st;
+            drop(alive, i);
           }
         }
-        drop(shrinking, i);
-        if (st != SVT_OK) {
+      }
+      if (alive.empty()) break;
+      // ---- fused update of every unfinished job: one launch ----
+      std::vector<UpdJob> uj;
+      for (int i : alive) {
+        svt_ctx* c = jobs[i];
+        const int nxt = 1 - c->ycur;
+        UpdJob u{};
+        u.row_ptr = c->row_ptr;
+        u.col_idx = c->col_idx;
+        u.csr_to_csc = c->csr_to_csc;
+        u.M = c->Mv;
+        u.y_in = ycur_csr(c);
+        u.y_out = c->Ycsr[nxt];
+        u.y_out_csc = c->Ycsc[nxt];
+        if (prec == 0) {
+          u.Ut = c->Ut;
+          u.V = c->Vf;
+          u.ldf = c->r;
+        } else {
+          u.Ut = c->Utf;
+          u.V = c->Vff;
+          u.ldf = c->ldf;
+        }
+        u.r = c->r;
+        u.m = (int)c->m;
+        u.delta = c->delta;
+        u.res2 = c->dscal;
+        uj.push_back(u);
+      }
+      TRY(batch_after_jobs(alive));
+      if (launch_sddmm_update_jobs(prec, uj.data(), (int)uj.size(), partial, cap, berr, bo.update_grid, bst) != 2)
+        return abort_all(fail(c0, SVT_ERR_CUDA, "batched update launch failed: %s",
+                              cudaGetErrorString(cudaGetLastError())));
+      batch_launches += 2;
+      for (int i : alive)
+        CU(jobs[i], cudaMemcpyAsync(jobs[i]->h_pin + 3 * kKMax, jobs[i]->dscal, sizeof(double), cudaMemcpyDeviceToHost,
+                                    bst));
+      CU(c0, cudaEventRecord(e1, bst));
+      CU(c0, cudaEventSynchronize(e1));
+      TRY(jobs_after_batch(alive));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      for (int i : std::vector<int>(alive)) {
+        svt_ctx* c = jobs[i];
+        const svt_status st = finish_step(c, c->r, c->h_pin[3 * kKMax], ms, nullptr);
+        svt_result& res = results[i];
+        res.iterations = c->k;
+        res.k0 = c->k0;
+        res.rank = c->r;
+        res.residual = std::sqrt(c->h_pin[3 * kKMax]) / c->normF;
+        res.norm2_M = c->norm2;
+        res.normF_M = c->normF;
+        res.ms = ms;
+        res.spmm_calls = c->total_spmm - spmm0[i];
+        res.lanczos_cycles = c->total_cycles - cyc0[i];
+        if (st == SVT_STOPPED) {
+          res.converged = 1;
+          status[i] = SVT_OK;
+          drop(alive, i);
+        } else if (st != SVT_OK) {
           status[i] = st;
+          drop(alive, i);
+        } else if (c->k >= c->opt.k_max) {
+          status[i] = fail(c, SVT_ERR_NOT_CONVERGED, "k_max iterations reached");
           drop(alive, i);
         }
       }
     }
-    if (alive.empty()) break;
-    // ---- fused update of every unfinished job: one launch ----
-    std::vector<UpdJob> uj;
-    for (int i : alive) {
-      svt_ctx* c = jobs[i];
-      const int nxt = 1 - c->ycur;
-      UpdJob u{};
-      u.row_ptr = c->row_ptr;
-      u.col_idx = c->col_idx;
-      u.csr_to_csc = c->csr_to_csc;
-      u.M = c->Mv;
-      u.y_in = ycur_csr(c);
-      u.y_out = c->Ycsr[nxt];
-      u.y_out_csc = c->Ycsc[nxt];
-      if (prec == 0) {
-        u.Ut = c->Ut;
-        u.V = c->Vf;
-        u.ldf = c->r;
-      } else {
-        u.Ut = c->Utf;
-        u.V = c->Vff;
-        u.ldf = c->ldf;
-      }
-      u.r = c->r;
-      u.m = (int)c->m;
-      u.delta = c->delta;
-      u.res2 = c->dscal;
-      uj.push_back(u);
-    }
-    TRY(batch_after_jobs(alive));
-    if (launch_sddmm_update_jobs(prec, uj.data(), (int)uj.size(), partial, cap, berr, bo.update_grid, bst) != 2)
-      return fail(c0, SVT_ERR_CUDA, "batched update launch failed: %s", cudaGetErrorString(cudaGetLastError()));
-    batch_launches += 2;
-    for (int i : alive)
-      CU(jobs[i], cudaMemcpyAsync(jobs[i]->h_pin + 3 * kKMax, jobs[i]->dscal, sizeof(double), cudaMemcpyDeviceToHost,
-                                  bst));
-    CU(c0, cudaEventRecord(e1, bst));
-    CU(c0, cudaEventSynchronize(e1));
-    TRY(jobs_after_batch(alive));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    for (int i : std::vector<int>(alive)) {
-      svt_ctx* c = jobs[i];
-      const svt_status st = finish_step(c, c->r, c->h_pin[3 * kKMax], ms, nullptr);
-      svt_result& res = results[i];
-      res.iterations = c->k;
-      res.k0 = c->k0;
-      res.rank = c->r;
-      res.residual = std::sqrt(c->h_pin[3 * kKMax]) / c->normF;
-      res.norm2_M = c->norm2;
-      res.normF_M = c->normF;
-      res.ms = ms;
-      res.spmm_calls = c->total_spmm - spmm0[i];
-      res.lanczos_cycles = c->total_cycles - cyc0[i];
-      if (st == SVT_STOPPED) {
-        res.converged = 1;
-        status[i] = SVT_OK;
-        drop(alive, i);
-      } else if (st != SVT_OK) {
-        status[i] = st;
-        drop(alive, i);
-      } else if (c->k >= c->opt.k_max) {
-        status[i] = fail(c, SVT_ERR_NOT_CONVERGED, "k_max iterations reached");
-        drop(alive, i);
-      }
-    }
-  }
+    return SVT_OK;
+  };
+  const svt_status fatal = run();
+  if (fatal != SVT_OK) return abort_all(fatal);
   c0->launches += batch_launches;
   for (int i = 0; i < n; ++i)
     if (status[i] != SVT_OK) return status[i] == SVT_ERR_NOT_CONVERGED ? SVT_ERR_NOT_CONVERGED : status[i];
