@@ -28,15 +28,20 @@ def _x_on_omega(s, p):
     return sample_X(p.rows, p.cols, U * d, V)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("fp32", 1e-4)])
-def test_shrink_matches_definition(cuda, precision, tol):
+@pytest.mark.parametrize("precision,lanczos_tol,tol,xtol", [("fp64", 0.0, 1e-9, 1e-6), ("fp64", 1e-9, 1e-9, 1e-8),
+                                                           ("fp32", 0.0, 1e-4, 1e-4)])
+def test_shrink_matches_definition(cuda, precision, lanczos_tol, tol, xtol):
+    """svt_shrink against D_tau of eq. (2.2) computed from a full SVD: the singular values above tau
+    to `tol` sigma_1 (Ritz values converge to second order in the residual) and X on Omega to xtol,
+    the Ritz-vector accuracy the Lanczos tolerance allows (float64 default 1e-7: X within 1e-6;
+    with lanczos_tol = 1e-9: within 1e-8)."""
     from paper_0810_3286_gb300 import Solver
     p = planted_problem(150, 110, 4, 4000, seed=2)
     tau = p.tau_default()
     # a dual iterate with its leading singular value at 1.6 tau: Y = c P_Omega(M)
     norm2 = osvt.spectral_norm(p.n1, p.n2, p.rows, p.cols, p.vals)
     y = 1.6 * tau / norm2 * p.vals
-    s = Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision)
+    s = Solver(p.n1, p.n2, p.rows, p.cols, p.vals, precision=precision, lanczos_tol=lanczos_tol)
     s.set_Y(y)
     r, sig = s.shrink(tau)
     U0, d0, V0, s_all = osvt.shrink(osvt.dense_from_omega(p.n1, p.n2, p.rows, p.cols, y), tau)
@@ -44,7 +49,9 @@ def test_shrink_matches_definition(cuda, precision, tol):
     assert np.abs(sig - (d0 + tau)).max() <= tol * s_all[0]
     x = _x_on_omega(s, p)
     x_ref = sample_X(p.rows, p.cols, U0 * d0, V0)
-    assert _per_iterate_error(x, x_ref, p.vals) <= (1e-8 if precision == "fp64" else 1e-4)
+    err = _per_iterate_error(x, x_ref, p.vals)
+    print("shrink %s lanczos_tol %g: X error %.2e" % (precision, lanczos_tol, err))
+    assert err <= xtol, err
     s.close()
 
 
