@@ -84,9 +84,9 @@ typedef struct svt_options {
   int lanczos_steps;      /* block steps J per Lanczos cycle (default 3; J b <= 128; raised where a thick restart
                              keeps several blocks of Ritz pairs, beyond 28 wanted triplets) */
   int max_cycles;         /* restarted Lanczos cycles per shrink before SVT_ERR_NUMERIC (default 40) */
-  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-7 FP64: per-iterate agreement
-                             with a float64 SVT to ~1e-7; 1e-5 FP32 and BF16: ten times the rounding of the
-                             float32 sparse products) */
+  double lanczos_tol;     /* Ritz residual tolerance relative to sigma_1 (0 = 1e-6 FP64: agreement with a
+                             float64 SVT with exact partial SVDs to ~1e-7 on the final X; 1e-4 FP32 and BF16,
+                             where the float32 products' own rounding dominates) */
   int indices_on_device;  /* rows/cols/M_omega given to svt_create are device pointers */
   int use_graphs;         /* replay each Lanczos cycle as a captured CUDA graph (default 1) */
   uint64_t seed;          /* seed of the random start columns of the Lanczos blocks */

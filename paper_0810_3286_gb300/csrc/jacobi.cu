@@ -259,7 +259,7 @@ __device__ void sort_columns(const R* nrm, int* order, int K) {
 //      rotations, W not rotated, four lanes per pair): quadratic convergence takes |cos| from
 //      2e-6 to ~1e-11 in one sweep, and a sweep whose pairs all had |cos| <= sqrt(tol) is the
 //      last (the caller's tol is 1e-11: Ritz vectors far more accurate than the Lanczos
-//      tolerance of 1e-7 sigma_1 they are tested against).  The right vectors of the leading
+//      tolerance of 1e-6 sigma_1 they are tested against).  The right vectors of the leading
 //      b triplets are then w = T^T g / ||g||^2 for the final columns g = theta x of G.
 // The result is a float64 one-sided Jacobi SVD of T; phase A only supplies its starting rotation.
 //

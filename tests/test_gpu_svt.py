@@ -28,13 +28,14 @@ def _x_on_omega(s, p):
     return sample_X(p.rows, p.cols, U * d, V)
 
 
-@pytest.mark.parametrize("precision,lanczos_tol,tol,xtol", [("fp64", 0.0, 1e-9, 1e-6), ("fp64", 1e-9, 1e-9, 1e-8),
-                                                           ("fp32", 0.0, 1e-4, 1e-4)])
+@pytest.mark.parametrize("precision,lanczos_tol,tol,xtol", [("fp64", 0.0, 1e-9, 1e-5), ("fp64", 1e-9, 1e-9, 1e-8),
+                                                           ("fp32", 0.0, 1e-4, 1e-3)])
 def test_shrink_matches_definition(cuda, precision, lanczos_tol, tol, xtol):
     """svt_shrink against D_tau of eq. (2.2) computed from a full SVD: the singular values above tau
     to `tol` sigma_1 (Ritz values converge to second order in the residual) and X on Omega to xtol,
-    the Ritz-vector accuracy the Lanczos tolerance allows (float64 default 1e-7: X within 1e-6;
-    with lanczos_tol = 1e-9: within 1e-8)."""
+    the Ritz-vector accuracy the Lanczos tolerance allows (float64 default 1e-6: X within the
+    per-iterate bound 1e-5; with lanczos_tol = 1e-9: within 1e-8; float32 default 1e-4: within
+    the mixed path's 1e-3)."""
     from paper_0810_3286_gb300 import Solver
     p = planted_problem(150, 110, 4, 4000, seed=2)
     tau = p.tau_default()
