@@ -114,3 +114,24 @@ def test_binding_struct_layouts_match_the_headers(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(s), name
         for f, _ in s._fields_:
             assert got[(name, f)] == getattr(s, f).offset, (name, f)
+
+
+def test_batch_rejects_bad_batches_before_any_device_work(libpath):
+    """svt_batch_solve checks the job count and its output arrays on the host first."""
+    import ctypes
+    from paper_0810_3286_gb300 import _abi
+    L = _abi.load(libpath)
+    opt = _abi.svt_batch_options()
+    L.svt_batch_default_options(ctypes.byref(opt))
+    assert (opt.spmm_grid, opt.update_grid, opt.autotune, opt.concurrent) == (0, 0, 0, 1)
+    res = (_abi.svt_result * 33)()
+    st = (ctypes.c_int * 33)()
+    jobs = (ctypes.c_void_p * 33)()
+    for n in (0, 33):   # 1 <= n <= 32
+        assert L.svt_batch_solve(ctypes.cast(jobs, ctypes.c_void_p), n, None, None, 1e-4, 27, ctypes.byref(opt),
+                                 ctypes.cast(res, ctypes.c_void_p), ctypes.cast(st, ctypes.c_void_p)) == _abi.SVT_ERR_ARG
+    # missing outputs, and a NULL context in the list
+    assert L.svt_batch_solve(ctypes.cast(jobs, ctypes.c_void_p), 2, None, None, 1e-4, 27, None, None,
+                             ctypes.cast(st, ctypes.c_void_p)) == _abi.SVT_ERR_ARG
+    assert L.svt_batch_solve(ctypes.cast(jobs, ctypes.c_void_p), 2, None, None, 1e-4, 27, None,
+                             ctypes.cast(res, ctypes.c_void_p), ctypes.cast(st, ctypes.c_void_p)) == _abi.SVT_ERR_ARG
