@@ -36,3 +36,20 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_traffic_is_reported_only_for_the_kernel_source_it_was_taken_on(tmp_path, monkeypatch):
+    """The DRAM traffic bench.py reports comes from the committed ncu summary of the same kernel
+    source (hash of csrc/) and precision; any other source or a missing class gives null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sha = bench._kernel_source_sha()
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps({"csrc_sha": sha, "classes_fp64": {"orth": 123.0}, "classes_fp32": {"orth": 45.0}}))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench._traffic_for("orth", "fp64") == 123.0
+    assert bench._traffic_for("orth", "fp32") == 45.0
+    assert bench._traffic_for("spmm", "fp64") is None
+    assert bench._traffic_for("orth", "bf16") is None
+    f.write_text(json.dumps({"csrc_sha": "0" * 16, "classes_fp64": {"orth": 123.0}}))
+    assert bench._traffic_for("orth", "fp64") is None
